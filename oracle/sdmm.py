@@ -1,0 +1,165 @@
+"""SDMM for the reweighted analysis problem (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Problem (§3.3 eq. delta): min ||W Psi^H x||_1  s.t. ||y - Phi x||_2 <= eps,
+x in R_+^N.  §4.3 eq. cvx2 splits it into f1(L1 x) + f2(L2 x) + f3(L3 x)
+with L1 = Psi^H, L2 = Phi, L3 = I, f1 = ||W .||_1, f2 = indicator of the
+l2 ball B around y, f3 = indicator of the positive orthant.  Algorithm 1
+(S = 3), step by step:
+
+  1  gamma > 0, x_hat(0), z_i(0) = 0
+  2  r_i(0) = L_i x_hat(0)
+  3  x_i(0) = L_i^H r_i(0)
+  4  for t = 1..T:
+  5      x_hat(t) = Q^{-1} sum_i x_i(t-1)                  (CG, ``cg``)
+  6      for i = 1..3:
+  7          r_i(t) = prox_{gamma f_i}(L_i x_hat(t) + z_i(t-1))
+  8          z_i(t) = z_i(t-1) + L_i x_hat(t) - r_i(t)
+  9          x_i(t) = L_i^H (r_i(t) - z_i(t))
+ 11      stop if the halting test holds
+
+Readings of what the paper leaves open (this build's choices):
+
+* x is kept complex, as in eq. cvx2 (x in C^N); the image is Re x_hat.
+* x_hat(0) = 0, so r_i(0) = 0 and x_i(0) = 0.
+* gamma = beta ||Psi^H Phi^H y||_inf with beta = 1e-3 (§4.4), the complex
+  modulus inside the max norm, computed once before t = 1.
+* Halting test of §4.4: zeta = |f1(t) - f1(t-1)| / |f1(t-1)| < xi = 1e-3 and
+  nu = ||y - Phi x_hat(t)|| / eps in [1 - tau, 1 + tau], tau = 0.1, with
+  f1(t) = f1(L1 x_hat(t)).  zeta is +inf while f1(t-1) = 0.  Parity runs use
+  a fixed T (``stop=False``); the quantities are still recorded.
+* CG: warm start from x_hat(t-1), ``cg_iters`` fixed steps.
+* Reweighting (§3.3 defers the rule to Candes et al. 2008): round 0 uses
+  w = 1; round r >= 1 uses w_j = delta_r / (delta_r + |alpha_j|) with
+  alpha = Psi^H x_hat at the end of round r-1 and
+  delta_r = max(10^-r ||alpha||_inf, 1e-6 ||alpha||_inf).  All SDMM state
+  (x_hat, z_i, x_i, gamma) carries over between rounds.
+
+Pinned by ``tests/test_oracle_sdmm.py``: the fixed point satisfies the
+constraints, and on a tiny problem the result approaches an independent
+constrained-minimisation solution of eq. delta.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable
+
+import numpy as np
+
+from . import cg as cg_mod
+from . import prox
+
+BETA = 1e-3
+XI = 1e-3
+TAU = 0.1
+
+
+@dataclasses.dataclass
+class Operators:
+    """The linear operators of eq. cvx2 (callables on complex128 arrays)."""
+
+    phi: Callable[[np.ndarray], np.ndarray]       # L2: C^N -> C^M
+    phi_adj: Callable[[np.ndarray], np.ndarray]   # L2^H
+    psi_adj: Callable[[np.ndarray], np.ndarray]   # L1 = Psi^H: C^N -> C^D
+    psi: Callable[[np.ndarray], np.ndarray]       # L1^H = Psi
+
+
+@dataclasses.dataclass
+class State:
+    """SDMM variables after iteration ``t``."""
+
+    x_hat: np.ndarray
+    z1: np.ndarray
+    z2: np.ndarray
+    z3: np.ndarray
+    x1: np.ndarray
+    x2: np.ndarray
+    x3: np.ndarray
+    gamma: float
+    t: int = 0
+    f1_prev: float = 0.0
+    history: list = dataclasses.field(default_factory=list)
+
+
+def penalty(ops: Operators, y: np.ndarray, beta: float = BETA) -> float:
+    """gamma = beta ||Psi^H Phi^H y||_inf (§4.4)."""
+    return float(beta * np.max(np.abs(ops.psi_adj(ops.phi_adj(y)))))
+
+
+def init_state(ops: Operators, y: np.ndarray, image_shape, beta: float = BETA) -> State:
+    """Algorithm 1 steps 1-3 with x_hat(0) = 0."""
+    x0 = np.zeros(image_shape, dtype=np.complex128)
+    r1 = ops.psi_adj(x0)
+    r2 = ops.phi(x0)
+    r3 = x0.copy()
+    return State(x_hat=x0, z1=np.zeros_like(r1), z2=np.zeros_like(r2), z3=np.zeros_like(r3),
+                 x1=ops.psi(r1), x2=ops.phi_adj(r2), x3=r3.copy(),
+                 gamma=penalty(ops, y, beta))
+
+
+def sdmm_iteration(ops: Operators, st: State, y: np.ndarray, eps: float, w: np.ndarray,
+                   cg_iters: int) -> dict:
+    """One pass of Algorithm 1 steps 5-9; updates ``st`` in place."""
+    def apply_q(v):
+        return ops.phi_adj(ops.phi(v)) + 2.0 * v
+
+    # step 5
+    b = st.x1 + st.x2 + st.x3
+    st.x_hat, cg_res = cg_mod.cg(apply_q, b, st.x_hat, cg_iters)
+    # steps 7-9, i = 1 (L1 = Psi^H, f1 = ||W .||_1)
+    s1 = ops.psi_adj(st.x_hat)
+    r1 = prox.soft_threshold(s1 + st.z1, st.gamma * w)
+    st.z1 = st.z1 + s1 - r1
+    st.x1 = ops.psi(r1 - st.z1)
+    # i = 2 (L2 = Phi, f2 = indicator of the l2 ball around y)
+    s2 = ops.phi(st.x_hat)
+    r2 = prox.project_l2_ball(s2 + st.z2, y, eps)
+    st.z2 = st.z2 + s2 - r2
+    st.x2 = ops.phi_adj(r2 - st.z2)
+    # i = 3 (L3 = I, f3 = indicator of the positive orthant)
+    s3 = st.x_hat
+    r3 = prox.project_positive(s3 + st.z3)
+    st.z3 = st.z3 + s3 - r3
+    st.x3 = r3 - st.z3
+    # halting quantities (§4.4)
+    f1 = float(np.sum(w * np.abs(s1)))
+    zeta = abs(f1 - st.f1_prev) / abs(st.f1_prev) if st.f1_prev != 0.0 else np.inf
+    nu = float(np.linalg.norm(y - s2) / eps)
+    st.f1_prev = f1
+    st.t += 1
+    rec = {"t": st.t, "f1": f1, "zeta": zeta, "nu": nu, "cg_residual": cg_res}
+    st.history.append(rec)
+    return rec
+
+
+def halted(rec: dict, xi: float = XI, tau: float = TAU) -> bool:
+    """The halting test of §4.4."""
+    return rec["zeta"] < xi and (1.0 - tau) <= rec["nu"] <= (1.0 + tau)
+
+
+def reweight(ops: Operators, x_hat: np.ndarray, round_index: int) -> np.ndarray:
+    """Weights of reweighting round ``round_index`` >= 1 (rule in the module docstring)."""
+    alpha = np.abs(ops.psi_adj(x_hat))
+    amax = float(alpha.max())
+    delta = max(10.0 ** (-round_index) * amax, 1e-6 * amax)
+    if delta == 0.0:
+        return np.ones_like(alpha)
+    return delta / (delta + alpha)
+
+
+def solve(ops: Operators, y: np.ndarray, eps: float, image_shape, coeff_shape,
+          iters: int, cg_iters: int, rounds: int = 1, stop: bool = False,
+          beta: float = BETA, weights: np.ndarray | None = None) -> State:
+    """``rounds`` reweighting rounds of ``iters`` SDMM iterations each."""
+    st = init_state(ops, y, image_shape, beta)
+    w = np.ones(coeff_shape) if weights is None else np.asarray(weights, dtype=np.float64)
+    for rnd in range(rounds):
+        if rnd > 0:
+            w = reweight(ops, st.x_hat, rnd)
+        for _ in range(iters):
+            rec = sdmm_iteration(ops, st, y, eps, w, cg_iters)
+            if stop and halted(rec):
+                break
+    st.weights = w
+    return st

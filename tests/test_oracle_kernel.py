@@ -1,0 +1,71 @@
+"""Pins of the oracle's Kaiser-Bessel kernel and unitary FFT (no GPU).
+
+The closed-form transform g_hat that D divides by (§5 eq. opmodel) is checked
+against numerical quadrature of g itself; the FFT (a library primitive inside
+the oracle) against the DFT written as a double loop.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import kaiser_bessel as kb
+from oracle import measurement as me
+
+
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
+@pytest.mark.parametrize("J", [2, 4, 6, 8])
+@pytest.mark.parametrize("f", [0.0, 0.03125, 0.1, 0.2, 0.25])
+def test_transform_matches_quadrature(J, f):
+    # g is even, so its transform is the cosine integral over [-J/2, J/2].
+    val, err = integrate.quad(lambda t: kb.kb_kernel(t, J) * np.cos(2 * np.pi * f * t),
+                              -J / 2, J / 2, epsabs=1e-14, epsrel=1e-14, limit=200)
+    assert abs(kb.kb_transform(f, J) - val) <= 1e-12 * abs(val)
+
+
+@pytest.mark.parametrize("J", [4, 6])
+def test_kernel_shape(J):
+    # Normalised to 1 at the centre, 1/I0(beta) at the support edge, zero outside.
+    beta = kb.kb_beta(J)
+    assert kb.kb_kernel(0.0, J) == pytest.approx(1.0, abs=1e-15)
+    assert kb.kb_kernel(J / 2, J) == pytest.approx(1.0 / np.i0(beta), rel=1e-14)
+    assert kb.kb_kernel(J / 2 + 1e-9, J) == 0.0
+    t = np.linspace(-J / 2, J / 2, 101)
+    assert np.allclose(kb.kb_kernel(t, J), kb.kb_kernel(-t, J), rtol=0, atol=1e-15)
+
+
+def test_beta_values():
+    # Beatty et al. (2005) shape rule at oversampling 2: beta(4) ~ 8.9962, beta(6) ~ 13.8551.
+    assert kb.kb_beta(4) == pytest.approx(8.99615, abs=1e-4)
+    assert kb.kb_beta(6) == pytest.approx(13.85510, abs=1e-4)
+
+
+def direct_dft2(g):
+    L0, L1 = g.shape
+    X = np.zeros_like(g, dtype=np.complex128)
+    for k0 in range(L0):
+        for k1 in range(L1):
+            s = 0j
+            for j0 in range(L0):
+                for j1 in range(L1):
+                    s += g[j0, j1] * np.exp(-2j * np.pi * (k0 * j0 / L0 + k1 * j1 / L1))
+            X[k0, k1] = s
+    return X / np.sqrt(L0 * L1)
+
+
+@pytest.mark.parametrize("L", [8, 12, 16, 24])
+def test_fft_against_direct_dft(L):
+    rng = np.random.default_rng(L)
+    g = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    X = me.fft2_unitary(g)
+    assert np.max(np.abs(X - direct_dft2(g))) <= 1e-13 * np.max(np.abs(X)) * L
+    # unitary: Parseval, and the inverse undoes it
+    assert np.linalg.norm(X) == pytest.approx(np.linalg.norm(g), rel=1e-13)
+    assert np.allclose(me.ifft2_unitary(X), g, rtol=0, atol=1e-13 * np.abs(g).max())
+
+
+def test_deapodisation_profile():
+    # g_hat(l / 2n) over l = -n/2..n/2-1: largest at l = 0, even about 0.
+    n = 64
+    gh = kb.deapodisation(n, 6)
+    assert np.argmax(gh) == n // 2
+    assert np.allclose(gh[1:], gh[1:][::-1], rtol=1e-14)

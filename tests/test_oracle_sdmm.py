@@ -1,0 +1,146 @@
+"""Pins of the oracle's SDMM (Algorithm 1) and its set-up (no GPU).
+
+* On tiny problems with one orthonormal basis, SDMM must reach the solution
+  of eq. delta found by an independent solver (SLSQP on a split
+  reformulation), in objective and constraint.
+* At a fixed point of Algorithm 1, L_i x_hat = r_i, which with steps 5 and 9
+  forces sum_i L_i^H z_i = 0; the dual variables must satisfy that.
+* On the 64 x 64 workload the iterates approach the constraint set of §4.4
+  (nu within [1 - tau, 1 + tau]), stay nearly real and non-negative, and SARA
+  beats the Dirac basis in SNR, the ordering §6 reports.
+* The noise model and l2 bound of §6.
+"""
+import numpy as np
+import pytest
+from scipy import optimize
+
+from oracle import measurement as me, sara, sdmm, simulate
+from paper_1307_4370_gb300 import inputs
+
+
+def tiny_problem(seed=11, n=8, J=4, M=40):
+    rng = np.random.default_rng(seed)
+    uv = inputs.uniform_uv(M, rng)
+    x_true = np.zeros((n, n))
+    idx = rng.choice(n * n, 5, replace=False)
+    x_true.ravel()[idx] = rng.uniform(0.5, 1, 5)
+    cols = []
+    for k in range(n * n):
+        e = np.zeros(n * n, complex)
+        e[k] = 1
+        cols.append(me.phi(e.reshape(n, n), uv, J))
+    A = np.array(cols).T
+    y0 = A @ x_true.ravel()
+    sig = simulate.noise_sigma(y0, 30.0)
+    y = y0 + sig * inputs.unit_complex_noise(M, rng)
+    return A, y, simulate.l2_bound(M, sig), n
+
+
+def dense_ops(A, Wm, n, q):
+    return sdmm.Operators(
+        phi=lambda x: A @ x.ravel(),
+        phi_adj=lambda v: (A.conj().T @ v).reshape(n, n),
+        psi_adj=lambda x: (Wm @ x.ravel()).reshape(q, n, n),
+        psi=lambda a: (Wm.T @ a.ravel()).reshape(n, n))
+
+
+def slsqp_reference(A, y, eps, Wm):
+    """min ||Wm x||_1 s.t. ||y - A x|| <= eps, x >= 0, with x = Wm^T (c+ - c-)."""
+    D = Wm.shape[0]
+    Ar = np.vstack([A.real, A.imag])
+    yr = np.concatenate([y.real, y.imag])
+    WT = Wm.T
+
+    def l2(v):
+        r = yr - Ar @ (WT @ (v[:D] - v[D:]))
+        return eps ** 2 - r @ r
+
+    res = optimize.minimize(lambda v: v.sum(), np.full(2 * D, 0.1), method="SLSQP",
+                            bounds=[(0, None)] * (2 * D),
+                            constraints=[{"type": "ineq", "fun": l2},
+                                         {"type": "ineq", "fun": lambda v: WT @ (v[:D] - v[D:])}],
+                            options={"maxiter": 3000, "ftol": 1e-14})
+    # SLSQP may stop on a line-search message at the optimum; require feasibility instead.
+    assert l2(res.x) >= -1e-9 * eps ** 2
+    assert np.min(WT @ (res.x[:D] - res.x[D:])) >= -1e-9
+    return res.fun
+
+
+@pytest.mark.parametrize("bases,levels", [((0,), 4), ((2,), 2), ((1,), 3)])
+def test_sdmm_reaches_constrained_minimum(bases, levels):
+    A, y, eps, n = tiny_problem()
+    Wm = np.array([sara.sara_analysis(np.eye(n * n)[k].reshape(n, n), levels, bases).ravel()
+                   for k in range(n * n)]).T.real
+    ops = dense_ops(A, Wm, n, len(bases))
+    st = sdmm.init_state(ops, y, (n, n))
+    w = np.ones((len(bases), n, n))
+    for _ in range(3000):
+        sdmm.sdmm_iteration(ops, st, y, eps, w, 10)
+    x = st.x_hat
+    assert np.max(np.abs(x.imag)) < 1e-8
+    assert x.real.min() > -1e-8
+    f_sdmm = np.abs(Wm @ x.real.ravel()).sum()
+    f_ref = slsqp_reference(A, y, eps, Wm)
+    assert f_sdmm == pytest.approx(f_ref, rel=1e-7)
+    assert np.linalg.norm(y - A @ x.real.ravel()) <= eps * (1 + 1e-7)
+    # fixed point: sum_i L_i^H z_i = 0
+    kkt = ops.psi(st.z1) + ops.phi_adj(st.z2) + st.z3
+    assert np.max(np.abs(kkt)) < 1e-6 * max(1.0, np.max(np.abs(st.z3)))
+
+
+def test_first_iteration_closed_form():
+    # x_hat(0) = 0 gives x_hat(1) = 0 (b = 0) and r2(1) = P_B(0): z2 = -P_B(0),
+    # x2(1) = Phi^H (2 P_B(0)) with P_B(0) = (1 - eps/||y||) y.
+    A, y, eps, n = tiny_problem()
+    Wm = np.eye(n * n)
+    ops = dense_ops(A, Wm, n, 1)
+    st = sdmm.init_state(ops, y, (n, n))
+    sdmm.sdmm_iteration(ops, st, y, eps, np.ones((1, n, n)), 10)
+    assert np.all(st.x_hat == 0)
+    pb0 = (1 - eps / np.linalg.norm(y)) * y
+    assert np.allclose(st.z2, -pb0, atol=1e-15)
+    assert np.allclose(st.x2, (A.conj().T @ (2 * pb0)).reshape(n, n), atol=1e-14)
+    assert st.gamma == pytest.approx(1e-3 * np.max(np.abs(A.conj().T @ y)))
+
+
+@pytest.fixture(scope="module")
+def sdmm64_runs():
+    p = inputs.make_problem("sdmm64")
+    w = p.workload
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db)
+    sa = sdmm.solve(simulate.operators(p.uv, w.n, w.J), y, eps, (w.n, w.n), (9, w.n, w.n),
+                    iters=50, cg_iters=10)
+    bp = sdmm.solve(simulate.operators(p.uv, w.n, w.J, bases=(0,)), y, eps, (w.n, w.n),
+                    (1, w.n, w.n), iters=50, cg_iters=10)
+    return p, sa, bp
+
+
+@pytest.mark.slow
+def test_sdmm64_constraint_and_ordering(sdmm64_runs):
+    p, sa, bp = sdmm64_runs
+    nus = [h["nu"] for h in sa.history]
+    assert nus[0] > 10                       # starts far outside the ball
+    assert all(0.85 <= v <= 1.1 for v in nus[-10:])
+    assert max(h["cg_residual"] for h in sa.history[-5:]) < 1e-6
+    x = sa.x_hat
+    assert np.max(np.abs(x.imag)) < 1e-2 * np.max(np.abs(x.real))
+    assert x.real.min() > -1e-2 * x.real.max()
+    assert simulate.snr_db(p.x_true, x.real) > simulate.snr_db(p.x_true, bp.x_hat.real) + 3.0
+
+
+def test_noise_model():
+    rng = np.random.default_rng(5)
+    M = 4096
+    y0 = inputs.random_vis(M, rng) * 3.0
+    sig = simulate.noise_sigma(y0, 30.0)
+    norms = []
+    for _ in range(200):
+        n_ = sig * inputs.unit_complex_noise(M, rng)
+        norms.append(np.linalg.norm(n_))
+    norms = np.array(norms)
+    # realised input SNR ~ 30 dB
+    assert 20 * np.log10(np.linalg.norm(y0) / np.mean(norms)) == pytest.approx(30.0, abs=0.05)
+    # eps^2 = (2M + 4 sqrt M) sigma^2 / 2 is the mean of ||n||^2 plus two standard deviations
+    eps = simulate.l2_bound(M, sig)
+    assert np.mean(norms <= eps) > 0.9
+    assert eps ** 2 == pytest.approx(M * sig ** 2 + 2 * np.sqrt(M) * sig ** 2, rel=1e-12)
