@@ -1,0 +1,264 @@
+/*
+ * purify.h -- C ABI of the GB300 (sm_103a) SDMM-SARA imaging library.
+ *
+ * The library computes the hot path of PURIFY (Carrillo, McEwen & Wiaux,
+ * arXiv:1307.4370): the measurement operator Phi = G F D Z of §5 eq. opmodel
+ * and its adjoint, the SARA dictionary of §3.3, the proximity operators of
+ * §4.4 eqs. prox1-prox3, the conjugate-gradient x-update of §4.4 and the
+ * SDMM iteration of Algorithm 1 for problem eq. delta.  Every numerical step
+ * runs in hand-written CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Complex vectors are interleaved float32 pairs (re, im) ("complex64").
+ * An image is n x n, row-major; element [r][c] is the pixel at offset
+ * l = (r - n/2, c - n/2).  A visibility frequency is a float32 pair
+ * (u0, u1) in radians per pixel, u0 paired with the row offset; Phi
+ * approximates (1/(2n)) sum_l x_l exp(-i u.l).  The oversampled grid is
+ * 2n x 2n; F is the unitary 2-D DFT; G interpolates with a Kaiser-Bessel
+ * kernel of J x J cells (J even, 2..8) whose first cell per axis is
+ * floor(kappa) - J/2 + 1, kappa = u 2n / (2 pi).
+ *
+ * SARA coefficients are q planes of n x n complex values, one per basis
+ * selected by bases_mask (bit 0 Dirac, bit p Daubechies-p, p = 1..8), in
+ * increasing bit order; each wavelet plane holds a periodic orthonormal
+ * DWT with `levels` levels in Mallat layout (low-low block top-left).  The
+ * dictionary is scaled by 1/sqrt(q) so that Psi Psi^H = I (§4.4 needs a
+ * Parseval frame for Q = Phi^H Phi + 2I).
+ *
+ * Memory and ownership
+ * --------------------
+ * Unless a parameter says otherwise, every array argument is a DEVICE
+ * pointer owned by the caller, on the device that was current when the
+ * context was created.  The library never frees caller memory.  A context
+ * owns its device scratch (the oversampled grid, the sorted visibility
+ * table, reduction buffers); an SDMM state owns its iteration variables.
+ * Scalars a call produces on the device are written to caller device
+ * pointers (never synchronously returned) unless the name says "host".
+ *
+ * Streams
+ * -------
+ * Every call that takes a purify_stream_t enqueues its work on that CUDA
+ * stream (a cudaStream_t; NULL = the legacy default stream) and returns
+ * without synchronising, except where noted.  Calls that use the same
+ * context or state must not overlap on the GPU: they share its scratch.
+ *
+ * Errors
+ * ------
+ * Every call returns a purify_status; PURIFY_OK is 0, failures are
+ * negative.  Argument checks happen before anything is enqueued; a call
+ * that fails an argument check has no effect.  PURIFY_E_CUDA reports an
+ * error from the CUDA runtime (launch or allocation), after which the
+ * context should be destroyed.  purify_status_string() names each code.
+ */
+#ifndef PURIFY_H
+#define PURIFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* purify_stream_t; /* same type as cudaStream_t */
+typedef struct purify_ctx purify_ctx;
+typedef struct purify_sdmm_state purify_sdmm_state;
+
+typedef enum {
+  PURIFY_OK = 0,
+  PURIFY_E_INVALID_ARG = -1,    /* NULL where an array is required, bad enum */
+  PURIFY_E_SIZE = -2,           /* a size outside the supported range */
+  PURIFY_E_NOT_DEVICE_PTR = -3, /* an argument that must be device memory is not */
+  PURIFY_E_ALLOC = -4,          /* device or host allocation failed */
+  PURIFY_E_CUDA = -5,           /* CUDA runtime error (launch, copy) */
+  PURIFY_E_TIMEOUT = -6,        /* a bounded device wait gave up */
+  PURIFY_E_UNSUPPORTED = -7     /* grid side with a prime factor other than 2, 3 */
+} purify_status;
+
+/* Visibility storage formats of the measured data y (SDMM data only). */
+typedef enum {
+  PURIFY_VIS_C64 = 0,       /* complex64 */
+  PURIFY_VIS_BF16_BLOCK = 1 /* bf16 (re, im) pairs, one float32 scale per 4096 */
+} purify_vis_format;
+
+/* Problem description (§3.1 eq. ri4, §5 eq. opmodel, §3.3).
+ *   n           image side; N = n*n; a multiple of 2^levels; 2n must factor
+ *               as 2^a 3^b with b <= 1; 8 <= n <= 4096.
+ *   M           number of visibilities, 1 <= M <= 2^31 - 1.
+ *   J           Kaiser-Bessel support per axis: 2, 4, 6 or 8.
+ *   oversample  must be 2 (§6 uses k = 2; the grid is 2n x 2n).
+ *   levels      wavelet levels of each Daubechies basis, 1..6 (4 in §6).
+ *   bases_mask  bit 0 Dirac, bit p db_p (p = 1..8); SARA is 0x1FF.  */
+typedef struct {
+  int32_t n;
+  int64_t M;
+  int32_t J;
+  int32_t oversample;
+  int32_t levels;
+  uint32_t bases_mask;
+} purify_desc;
+
+/* Create a context for one u-v coverage (§5: G depends only on the
+ * frequencies, so it is set up once).  uv holds M float32 pairs and may be
+ * a host or a device pointer; it is read during the call and not kept.
+ * Set-up sorts the visibilities by grid tile and builds the tile lists of
+ * the gridding adjoint; this call synchronises `stream`.
+ * *out receives the context, or NULL on failure. */
+int purify_create(purify_ctx** out, const purify_desc* desc, const float* uv,
+                  purify_stream_t stream);
+
+/* Release a context and its device memory (synchronises the device). */
+void purify_destroy(purify_ctx* ctx);
+
+/* Name of a status code (static string). */
+const char* purify_status_string(int status);
+
+/* Sizes of a context: N = n*n, M, q = number of bases, D = q*N. */
+int purify_sizes(const purify_ctx* ctx, int64_t* N, int64_t* M, int32_t* q,
+                 int64_t* D);
+
+/* y = Phi x (§5 eq. opmodel with B = I): x is N complex64 (device), y is M
+ * complex64 (device), visibilities in the order of the uv array given to
+ * purify_create. */
+int purify_phi(purify_ctx* ctx, const float* x, float* y, purify_stream_t stream);
+
+/* x = Phi^H y = Z^T D F^H G^T y: y is M complex64, x is N complex64. */
+int purify_phi_adj(purify_ctx* ctx, const float* y, float* x, purify_stream_t stream);
+
+/* alpha = Psi^H x (§3.3, §4.3 L1 = Psi^H): x is N complex64, alpha is D
+ * complex64 (q planes of n x n). */
+int purify_sara_analysis(purify_ctx* ctx, const float* x, float* alpha,
+                         purify_stream_t stream);
+
+/* x = Psi alpha: alpha is D complex64, x is N complex64. */
+int purify_sara_synthesis(purify_ctx* ctx, const float* alpha, float* x,
+                          purify_stream_t stream);
+
+/* Weighted complex soft threshold, the prox of gamma ||W .||_1 (§4.4 eq.
+ * prox1): out_j = a_j/|a_j| (|a_j| - gamma w_j)^+ (0 where a_j = 0).
+ * in, out: `count` complex64 (may alias); w: `count` float32 weights >= 0,
+ * or NULL for w = 1. */
+int purify_prox_l1_reweighted(purify_ctx* ctx, int64_t count, const float* in,
+                              const float* w, float gamma, float* out,
+                              purify_stream_t stream);
+
+/* Projection onto the l2 ball B = {r : ||r - y||_2 <= eps} of §4.3 (the
+ * formula printed as eq. prox2 is read as this projection):
+ * out = y + min(1, eps/||in - y||) (in - y).  in, y, out: `count`
+ * complex64 (in and out may alias).  ||in - y|| is accumulated in FP64
+ * and written to *norm_out (a device double) when norm_out is not NULL. */
+int purify_proj_l2ball(purify_ctx* ctx, int64_t count, const float* in,
+                       const float* y, double eps, float* out, double* norm_out,
+                       purify_stream_t stream);
+
+/* Projection onto the positive orthant of §4.4 eq. prox3, complex vectors
+ * treated as real pairs (§4.1): out = max(Re in, 0) + 0i.  May alias. */
+int purify_proj_positive(purify_ctx* ctx, int64_t count, const float* in,
+                         float* out, purify_stream_t stream);
+
+/* `iters` conjugate-gradient steps on Q x = b, Q = Phi^H Phi + 2I (§4.4),
+ * starting from the x passed in (overwritten with the result).  b and x are
+ * N complex64.  Inner products and step sizes are FP64.  When resid_out is
+ * not NULL the recurrence residual ||r|| is written there (device double). */
+int purify_cg_solve(purify_ctx* ctx, const float* b, float* x, int32_t iters,
+                    double* resid_out, purify_stream_t stream);
+
+/* SDMM parameters (§4.4). */
+typedef struct {
+  int32_t max_iters;  /* T_max per reweighting round */
+  int32_t cg_iters;   /* CG steps per x-update */
+  int32_t rounds;     /* reweighting rounds (1 = no reweighting) */
+  int32_t check_every;/* evaluate the halting test every this many
+                         iterations (needs one 48-byte device-to-host copy);
+                         0 = never (run exactly max_iters per round) */
+  double beta;        /* gamma = beta ||Psi^H Phi^H y||_inf; 1e-3 in §4.4 */
+  double xi;          /* bound on the relative change of f1; 1e-3 */
+  double tau;         /* tolerance on nu = ||y - Phi x||/eps; 0.1 */
+} purify_sdmm_params;
+
+/* Defaults of §4.4: T = 300, k = 10, 1 round, no halting checks,
+ * beta = xi = 1e-3, tau = 0.1. */
+void purify_sdmm_default_params(purify_sdmm_params* p);
+
+/* Halting quantities after the last iteration (§4.4). */
+typedef struct {
+  int64_t iters;      /* SDMM iterations run so far */
+  double f1;          /* ||W Psi^H x_hat||_1 */
+  double zeta;        /* |f1(t) - f1(t-1)| / |f1(t-1)| (inf while f1(t-1) = 0) */
+  double nu;          /* ||y - Phi x_hat|| / eps */
+  double gamma;       /* penalty parameter */
+  double cg_residual; /* CG recurrence residual of the last x-update */
+} purify_report;
+
+/* Allocate the iteration variables of Algorithm 1 for a context. */
+int purify_sdmm_state_create(purify_ctx* ctx, purify_sdmm_state** out);
+void purify_sdmm_state_destroy(purify_sdmm_state* st);
+
+/* Load the data: y (M complex64, HOST or DEVICE pointer, in uv order) and
+ * eps; resets the state to Algorithm 1 steps 1-3 with x_hat(0) = 0 and
+ * weights w = 1, and computes gamma = beta ||Psi^H Phi^H y||_inf. */
+int purify_sdmm_init(purify_ctx* ctx, purify_sdmm_state* st, const float* y,
+                     double eps, const purify_sdmm_params* params,
+                     purify_stream_t stream);
+
+/* Replace the data vector y (HOST or DEVICE pointer) without touching the
+ * iteration variables. */
+int purify_sdmm_set_data(purify_ctx* ctx, purify_sdmm_state* st, const float* y,
+                         purify_stream_t stream);
+
+/* Replace the data vector y (HOST or DEVICE complex64, caller order) and keep
+ * it in the state as bf16 (re, im) pairs with one float32 scale per block of
+ * 4096 visibilities of the library's internal visibility order:
+ * scale_b = max |component| over the block (1 if the block is zero), stored
+ * value = round-to-nearest-even bf16 of component / scale_b.  The l2 branch
+ * of the SDMM step (the only reader of y) then reads 4 bytes per visibility
+ * instead of 8; its norms stay FP64. */
+int purify_sdmm_set_data_bf16(purify_ctx* ctx, purify_sdmm_state* st, const float* y,
+                              purify_stream_t stream);
+
+/* One SDMM iteration (Algorithm 1 steps 5-9). */
+int purify_sdmm_step(purify_ctx* ctx, purify_sdmm_state* st, purify_stream_t stream);
+
+/* Start a new reweighting round (§3.3): w_j = delta / (delta + |alpha_j|),
+ * alpha = Psi^H x_hat, delta = max(10^-round ||alpha||_inf,
+ * 1e-6 ||alpha||_inf); round >= 1.  Iteration variables carry over. */
+int purify_sdmm_reweight(purify_ctx* ctx, purify_sdmm_state* st, int32_t round,
+                         purify_stream_t stream);
+
+/* Set the weights directly (D float32, device pointer). */
+int purify_sdmm_set_weights(purify_ctx* ctx, purify_sdmm_state* st, const float* w,
+                            purify_stream_t stream);
+
+/* Copy x_hat (N complex64) to x_out, a HOST or DEVICE pointer.  A host copy
+ * synchronises `stream`. */
+int purify_sdmm_get_image(purify_ctx* ctx, purify_sdmm_state* st, float* x_out,
+                          purify_stream_t stream);
+
+/* Read the halting quantities (synchronises `stream`). */
+int purify_sdmm_get_report(purify_ctx* ctx, purify_sdmm_state* st,
+                           purify_report* report, purify_stream_t stream);
+
+/* Run the whole method: init, then `rounds` reweighting rounds of up to
+ * max_iters iterations, stopping a round early when check_every > 0 and
+ * the halting test of §4.4 holds.  y: HOST or DEVICE; x_out: HOST or
+ * DEVICE.  Synchronises `stream` before returning. */
+int purify_sdmm_solve(purify_ctx* ctx, const float* y, double eps,
+                      const purify_sdmm_params* params, float* x_out,
+                      purify_report* report, purify_stream_t stream);
+
+/* Checkpoint / resume: the variables (x_hat, r, p, z1, z2, z3, x1, w and the
+ * scalars) as one opaque byte blob.  purify_sdmm_state_bytes gives its size;
+ * export writes it to a HOST buffer, import reads one back (same context
+ * sizes).  Both synchronise `stream`. */
+int purify_sdmm_state_bytes(purify_ctx* ctx, size_t* bytes);
+int purify_sdmm_export(purify_ctx* ctx, purify_sdmm_state* st, void* host_buf,
+                       size_t bytes, purify_stream_t stream);
+int purify_sdmm_import(purify_ctx* ctx, purify_sdmm_state* st, const void* host_buf,
+                       size_t bytes, purify_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PURIFY_H */

@@ -1,0 +1,371 @@
+"""Thin Python binding of the C ABI in include/purify.h (argument marshalling only).
+
+Every function here forwards to the CUDA library of the same name; tensors are
+passed as device pointers (``data_ptr()``) together with the current torch CUDA
+stream.  There is no fallback: if the library is missing or cannot be loaded,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+PURIFY_OK = 0
+STATUS_NAMES = {
+    0: "PURIFY_OK", -1: "PURIFY_E_INVALID_ARG", -2: "PURIFY_E_SIZE", -3: "PURIFY_E_NOT_DEVICE_PTR",
+    -4: "PURIFY_E_ALLOC", -5: "PURIFY_E_CUDA", -6: "PURIFY_E_TIMEOUT", -7: "PURIFY_E_UNSUPPORTED",
+}
+SARA_MASK = 0x1FF
+
+
+class PurifyError(RuntimeError):
+    """A negative status from the library."""
+
+    def __init__(self, func: str, status: int):
+        self.status = status
+        msg = _LIB.purify_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{func} failed: {STATUS_NAMES.get(status, status)} ({msg})")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("M", ctypes.c_int64), ("J", ctypes.c_int32),
+                ("oversample", ctypes.c_int32), ("levels", ctypes.c_int32), ("bases_mask", ctypes.c_uint32)]
+
+
+class SdmmParams(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("cg_iters", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("beta", ctypes.c_double), ("xi", ctypes.c_double),
+                ("tau", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("f1", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("nu", ctypes.c_double), ("gamma", ctypes.c_double), ("cg_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_SIGS = {
+    "purify_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Desc), _vp, _vp]),
+    "purify_destroy": (None, [_vp]),
+    "purify_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_i64)]),
+    "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_phi_adj": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sara_analysis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sara_synthesis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_prox_l1_reweighted": (ctypes.c_int, [_vp, _i64, _vp, _vp, ctypes.c_float, _vp, _vp]),
+    "purify_proj_l2ball": (ctypes.c_int, [_vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    "purify_proj_positive": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp]),
+    "purify_cg_solve": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "purify_sdmm_default_params": (None, [ctypes.POINTER(SdmmParams)]),
+    "purify_sdmm_state_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "purify_sdmm_state_destroy": (None, [_vp]),
+    "purify_sdmm_init": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(SdmmParams), _vp]),
+    "purify_sdmm_set_data": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sdmm_set_data_bf16": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sdmm_step": (ctypes.c_int, [_vp, _vp, _vp]),
+    "purify_sdmm_reweight": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
+    "purify_sdmm_set_weights": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sdmm_get_image": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_sdmm_get_report": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(Report), _vp]),
+    "purify_sdmm_solve": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.POINTER(SdmmParams), _vp,
+                                         ctypes.POINTER(Report), _vp]),
+    "purify_sdmm_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "purify_sdmm_export": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "purify_sdmm_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(func: str, status: int) -> None:
+    if status != PURIFY_OK:
+        raise PurifyError(func, status)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    return int(t)
+
+
+def _c64(t: torch.Tensor, n: int, what: str) -> torch.Tensor:
+    if t.dtype != torch.complex64 or not t.is_cuda or t.numel() != n:
+        raise ValueError(f"{what}: expected {n} complex64 values on a CUDA device, got "
+                         f"{t.dtype} {tuple(t.shape)} on {t.device}")
+    return t.contiguous()
+
+
+# ---------------------------------------------------------------------------
+# Raw functions with the C names (pointer-level)
+# ---------------------------------------------------------------------------
+def purify_create(desc: Desc, uv_ptr: int, stream=None) -> int:
+    lib = load()
+    out = _vp()
+    _check("purify_create", lib.purify_create(ctypes.byref(out), ctypes.byref(desc), uv_ptr, _stream(stream)))
+    return out.value
+
+
+def purify_destroy(ctx: int) -> None:
+    load().purify_destroy(ctx)
+
+
+class Context:
+    """A measurement set-up (u-v coverage, image side, kernel, dictionary).
+
+    Methods are named after the C entry points without the ``purify_`` prefix
+    and take / return torch complex64 tensors on the context's device.
+    """
+
+    def __init__(self, n: int, uv, J: int = 6, levels: int = 4, bases_mask: int = SARA_MASK,
+                 device=None):
+        self.lib = load()
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        uv_t = torch.as_tensor(uv, dtype=torch.float32)
+        if uv_t.dim() != 2 or uv_t.shape[1] != 2:
+            raise ValueError("uv must be (M, 2)")
+        uv_t = uv_t.contiguous()
+        self.M = int(uv_t.shape[0])
+        self.n = int(n)
+        self.J = int(J)
+        self.levels = int(levels)
+        self.bases_mask = int(bases_mask)
+        self.q = bin(self.bases_mask & 0x1FF).count("1")
+        self.N = self.n * self.n
+        self.D = self.q * self.N
+        desc = Desc(self.n, self.M, self.J, 2, self.levels, self.bases_mask)
+        uv_keep = uv_t if uv_t.is_cuda else uv_t.numpy()
+        self.ctx = purify_create(desc, _ptr(uv_keep))
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            purify_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _img(self, shape=None):
+        return torch.empty(self.N if shape is None else shape, dtype=torch.complex64, device=self.device)
+
+    # operators -----------------------------------------------------------
+    def phi(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = _c64(x, self.N, "x")
+        y = out if out is not None else torch.empty(self.M, dtype=torch.complex64, device=self.device)
+        _check("purify_phi", self.lib.purify_phi(self.ctx, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def phi_adj(self, y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        y = _c64(y, self.M, "y")
+        x = out if out is not None else self._img((self.n, self.n))
+        _check("purify_phi_adj", self.lib.purify_phi_adj(self.ctx, _ptr(y), _ptr(x), _stream(stream)))
+        return x
+
+    def sara_analysis(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = _c64(x, self.N, "x")
+        a = out if out is not None else self._img((self.q, self.n, self.n))
+        _check("purify_sara_analysis", self.lib.purify_sara_analysis(self.ctx, _ptr(x), _ptr(a), _stream(stream)))
+        return a
+
+    def sara_synthesis(self, alpha: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        alpha = _c64(alpha, self.D, "alpha")
+        x = out if out is not None else self._img((self.n, self.n))
+        _check("purify_sara_synthesis",
+               self.lib.purify_sara_synthesis(self.ctx, _ptr(alpha), _ptr(x), _stream(stream)))
+        return x
+
+    def prox_l1_reweighted(self, a: torch.Tensor, w: torch.Tensor | None, gamma: float,
+                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        out = out if out is not None else torch.empty_like(a)
+        if w is not None and (w.dtype != torch.float32 or w.numel() != a.numel()):
+            raise ValueError("w: float32, one weight per entry")
+        _check("purify_prox_l1_reweighted",
+               self.lib.purify_prox_l1_reweighted(self.ctx, a.numel(), _ptr(a.contiguous()), _ptr(w),
+                                                  float(gamma), _ptr(out), _stream(stream)))
+        return out
+
+    def proj_l2ball(self, r: torch.Tensor, y: torch.Tensor, eps: float, out: torch.Tensor | None = None,
+                    norm_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        out = out if out is not None else torch.empty_like(r)
+        _check("purify_proj_l2ball",
+               self.lib.purify_proj_l2ball(self.ctx, r.numel(), _ptr(r.contiguous()), _ptr(y.contiguous()),
+                                           float(eps), _ptr(out), _ptr(norm_out), _stream(stream)))
+        return out
+
+    def proj_positive(self, a: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        out = out if out is not None else torch.empty_like(a)
+        _check("purify_proj_positive",
+               self.lib.purify_proj_positive(self.ctx, a.numel(), _ptr(a.contiguous()), _ptr(out),
+                                             _stream(stream)))
+        return out
+
+    def cg_solve(self, b: torch.Tensor, x0: torch.Tensor, iters: int, stream=None):
+        """Returns (x, residual) after ``iters`` CG steps on (Phi^H Phi + 2I) x = b."""
+        b = _c64(b, self.N, "b")
+        x = _c64(x0, self.N, "x0").clone()
+        res = torch.zeros(1, dtype=torch.float64, device=self.device)
+        _check("purify_cg_solve",
+               self.lib.purify_cg_solve(self.ctx, _ptr(b), _ptr(x), int(iters), _ptr(res), _stream(stream)))
+        return x, res
+
+    # SDMM ----------------------------------------------------------------
+    def sdmm_state(self) -> "SdmmState":
+        return SdmmState(self)
+
+    def sdmm_solve(self, y, eps: float, max_iters: int = 300, cg_iters: int = 10, rounds: int = 1,
+                   check_every: int = 0, beta: float = 1e-3, xi: float = 1e-3, tau: float = 0.1,
+                   out=None, stream=None):
+        """Whole solve; y and out may be host (numpy / CPU tensor) or device tensors."""
+        p = default_params()
+        p.max_iters, p.cg_iters, p.rounds, p.check_every = max_iters, cg_iters, rounds, check_every
+        p.beta, p.xi, p.tau = beta, xi, tau
+        if out is None:
+            out = self._img((self.n, self.n))
+        rep = Report()
+        _check("purify_sdmm_solve",
+               self.lib.purify_sdmm_solve(self.ctx, _ptr(y), float(eps), ctypes.byref(p), _ptr(out),
+                                          ctypes.byref(rep), _stream(stream)))
+        return out, rep.as_dict()
+
+
+def default_params() -> SdmmParams:
+    p = SdmmParams()
+    load().purify_sdmm_default_params(ctypes.byref(p))
+    return p
+
+
+class SdmmState:
+    """Iteration variables of Algorithm 1 on a context."""
+
+    def __init__(self, ctx: Context):
+        self.c = ctx
+        self.lib = ctx.lib
+        out = _vp()
+        _check("purify_sdmm_state_create", self.lib.purify_sdmm_state_create(ctx.ctx, ctypes.byref(out)))
+        self.st = out.value
+
+    def close(self) -> None:
+        if getattr(self, "st", None):
+            self.lib.purify_sdmm_state_destroy(self.st)
+            self.st = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, y, eps: float, cg_iters: int = 10, beta: float = 1e-3, max_iters: int = 300,
+             rounds: int = 1, stream=None) -> None:
+        p = default_params()
+        p.cg_iters, p.beta, p.max_iters, p.rounds = cg_iters, beta, max_iters, rounds
+        _check("purify_sdmm_init", self.lib.purify_sdmm_init(self.c.ctx, self.st, _ptr(y), float(eps),
+                                                             ctypes.byref(p), _stream(stream)))
+
+    def set_data(self, y, stream=None) -> None:
+        _check("purify_sdmm_set_data", self.lib.purify_sdmm_set_data(self.c.ctx, self.st, _ptr(y),
+                                                                     _stream(stream)))
+
+    def set_data_bf16(self, y, stream=None) -> None:
+        _check("purify_sdmm_set_data_bf16",
+               self.lib.purify_sdmm_set_data_bf16(self.c.ctx, self.st, _ptr(y), _stream(stream)))
+
+    def step(self, stream=None) -> None:
+        _check("purify_sdmm_step", self.lib.purify_sdmm_step(self.c.ctx, self.st, _stream(stream)))
+
+    def reweight(self, round_index: int, stream=None) -> None:
+        _check("purify_sdmm_reweight",
+               self.lib.purify_sdmm_reweight(self.c.ctx, self.st, int(round_index), _stream(stream)))
+
+    def set_weights(self, w: torch.Tensor, stream=None) -> None:
+        if w.dtype != torch.float32 or w.numel() != self.c.D or not w.is_cuda:
+            raise ValueError("w: D float32 values on the device")
+        _check("purify_sdmm_set_weights",
+               self.lib.purify_sdmm_set_weights(self.c.ctx, self.st, _ptr(w.contiguous()), _stream(stream)))
+
+    def get_image(self, out=None, stream=None):
+        if out is None:
+            out = self.c._img((self.c.n, self.c.n))
+        _check("purify_sdmm_get_image", self.lib.purify_sdmm_get_image(self.c.ctx, self.st, _ptr(out),
+                                                                       _stream(stream)))
+        return out
+
+    def report(self, stream=None) -> dict:
+        rep = Report()
+        _check("purify_sdmm_get_report",
+               self.lib.purify_sdmm_get_report(self.c.ctx, self.st, ctypes.byref(rep), _stream(stream)))
+        return rep.as_dict()
+
+    def export(self, stream=None) -> bytes:
+        nb = ctypes.c_size_t()
+        _check("purify_sdmm_state_bytes", self.lib.purify_sdmm_state_bytes(self.c.ctx, ctypes.byref(nb)))
+        buf = ctypes.create_string_buffer(nb.value)
+        _check("purify_sdmm_export",
+               self.lib.purify_sdmm_export(self.c.ctx, self.st, buf, nb.value, _stream(stream)))
+        return buf.raw
+
+    def import_(self, blob: bytes, stream=None) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check("purify_sdmm_import",
+               self.lib.purify_sdmm_import(self.c.ctx, self.st, buf, len(blob), _stream(stream)))
+
+
+def l2_bound(M: int, sigma: float) -> float:
+    """eps = sqrt((2M + 4 sqrt M) sigma^2 / 2), the chi^2 bound of §6."""
+    return math.sqrt((2.0 * M + 4.0 * math.sqrt(M)) * sigma * sigma / 2.0)

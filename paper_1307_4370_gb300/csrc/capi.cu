@@ -1,0 +1,817 @@
+// C ABI of the library (include/purify.h): context set-up, the operator
+// calls, the conjugate-gradient solve and the SDMM driver of Algorithm 1.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace purify;
+
+namespace purify {
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? PURIFY_OK : PURIFY_E_CUDA; }
+
+}  // namespace purify
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define TRY(expr)                  \
+  do {                             \
+    int _st = (expr);              \
+    if (_st != PURIFY_OK) return _st; \
+  } while (0)
+
+#define TRY_CUDA(expr) TRY(check_cuda(expr))
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+int dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PURIFY_E_ALLOC;
+  }
+  return PURIFY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kaiser-Bessel: beta of Beatty et al. (2005) for oversampling 2, the kernel
+// g(t) = I0(beta sqrt(1 - (2t/J)^2)) / I0(beta) and its closed-form transform.
+// ---------------------------------------------------------------------------
+double kb_beta(int J) {
+  const double a = 2.0;
+  return M_PI * std::sqrt((J / a) * (J / a) * (a - 0.5) * (a - 0.5) - 0.8);
+}
+
+double kb_g(double t, int J, double beta, double i0b) {
+  const double s = 2.0 * t / J;
+  if (std::fabs(s) > 1.0) return 0.0;
+  return std::cyl_bessel_i(0.0, beta * std::sqrt(std::max(0.0, 1.0 - s * s))) / i0b;
+}
+
+double kb_ghat(double f, int J, double beta, double i0b) {
+  const double a = std::sqrt(beta * beta - (M_PI * J * f) * (M_PI * J * f));
+  return J * std::sinh(a) / (i0b * a);
+}
+
+// Solve V c = f (Gaussian elimination with partial pivoting, long double).
+void solve_dense(std::vector<long double>& A, std::vector<long double>& b, int n) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs((double)A[i * n + k]) > std::fabs((double)A[piv * n + k])) piv = i;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+      std::swap(b[k], b[piv]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const long double f = A[i * n + k] / A[k * n + k];
+      for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    long double s = b[k];
+    for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * b[j];
+    b[k] = s / A[k * n + k];
+  }
+}
+
+// Fit each tap's weight, as a function of z = 2x - 1 on [-1, 1], by the
+// polynomial interpolating it at Chebyshev nodes; take the lowest degree
+// whose float Horner evaluation is within 1.5e-7 of the double kernel.
+KbPoly fit_kb(int J) {
+  const double beta = kb_beta(J);
+  const double i0b = std::cyl_bessel_i(0.0, beta);
+  KbPoly kb{};
+  kb.J = J;
+  for (int deg = 6; deg <= kMaxKbDeg; ++deg) {
+    const int np = deg + 1;
+    float err = 0.f;
+    for (int a = 0; a < J; ++a) {
+      std::vector<long double> A(np * np), f(np);
+      for (int i = 0; i < np; ++i) {
+        const long double z = std::cos(M_PI * (i + 0.5) / np);
+        const double x = 0.5 * ((double)z + 1.0);
+        long double zp = 1.0L;
+        for (int j = 0; j < np; ++j) {
+          A[i * np + j] = zp;
+          zp *= z;
+        }
+        f[i] = kb_g(x + J / 2 - 1 - a, J, beta, i0b);
+      }
+      solve_dense(A, f, np);
+      for (int j = 0; j < np; ++j) kb.c[a][j] = (float)f[j];
+      for (int t = 0; t <= 4000; ++t) {
+        const double x = t / 4000.0 * (1.0 - 1e-12);
+        const float z = std::fma(2.0f, (float)x, -1.0f);
+        float acc = kb.c[a][deg];
+        for (int k = deg - 1; k >= 0; --k) acc = std::fma(acc, z, kb.c[a][k]);
+        err = std::max(err, (float)std::fabs(acc - kb_g(x + J / 2 - 1 - a, J, beta, i0b)));
+      }
+    }
+    kb.deg = deg;
+    kb.max_err = err;
+    if (err <= 1.5e-7f) break;
+  }
+  return kb;
+}
+
+FftPlan make_plan(int L) {
+  FftPlan p{};
+  p.L = L;
+  int rest = L;
+  if (rest % 3 == 0) {
+    p.radix[p.nst++] = 3;
+    rest /= 3;
+    while (rest % 4 == 0) { p.radix[p.nst++] = 4; rest /= 4; }
+    if (rest % 2 == 0) { p.radix[p.nst++] = 2; rest /= 2; }
+  } else {
+    while (rest % 8 == 0) { p.radix[p.nst++] = 8; rest /= 8; }
+    if (rest % 4 == 0) { p.radix[p.nst++] = 4; rest /= 4; }
+    if (rest % 2 == 0) { p.radix[p.nst++] = 2; rest /= 2; }
+  }
+  if (rest != 1) p.nst = -1;
+  return p;
+}
+
+bool good_side(int L) {
+  int r = L;
+  int threes = 0;
+  while (r % 3 == 0) { r /= 3; ++threes; }
+  while (r % 2 == 0) r /= 2;
+  return r == 1 && threes <= 1;
+}
+
+// First footprint cell of every visibility (same arithmetic as the kernels).
+__global__ void k_footprint(const float2* __restrict__ uv, int64_t M, KappaScale ks, int J, int L,
+                            int2* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+    int kr, kc;
+    float fr, fc;
+    split_kappa(uv[i].x, ks, kr, fr);
+    split_kappa(uv[i].y, ks, kc, fc);
+    out[i] = make_int2(wrap(kr - (J / 2 - 1), L), wrap(kc - (J / 2 - 1), L));
+  }
+}
+
+__global__ void k_fill_f32(int64_t n, float* p, float v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_scatter_perm(int64_t n, const float2* __restrict__ src, const int* __restrict__ perm,
+                               float2* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[i]] = src[i];
+}
+
+__global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ src, const int* __restrict__ perm,
+                             uint32_t* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+
+__global__ void k_sqrt_to(const double* src, double* dst) { *dst = sqrt(*src); }
+
+unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
+
+void free_ctx(purify_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_off, c->d_tile_list, c->d_tile_order,
+                  c->d_grid, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
+                  c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  delete c;
+}
+
+// Visibility table: sort by the grid tile of the first footprint cell and
+// list, per tile, every visibility whose J x J footprint meets it.
+int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
+  const int64_t M = c->M;
+  float2* d_uv_user = nullptr;
+  int2* d_k0 = nullptr;
+  int st = PURIFY_OK;
+  TRY(dev_alloc(&d_uv_user, M));
+  if ((st = dev_alloc(&d_k0, M)) != PURIFY_OK) { cudaFree(d_uv_user); return st; }
+  cudaMemcpyAsync(d_uv_user, uv_in, M * sizeof(float2), cudaMemcpyDefault, s);
+  k_footprint<<<nblk(M), 256, 0, s>>>(d_uv_user, M, c->ks, c->J, c->L, d_k0);
+  std::vector<int2> k0(M);
+  cudaMemcpyAsync(k0.data(), d_k0, M * sizeof(int2), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(d_uv_user);
+    cudaFree(d_k0);
+    return PURIFY_E_CUDA;
+  }
+  const int T = c->tileT, TD = c->tiles_1d, J = c->J, L = c->L;
+  // counting sort by home tile (stable: keeps the caller's order inside a tile)
+  std::vector<int> cnt(c->ntiles + 1, 0), perm(M);
+  for (int64_t i = 0; i < M; ++i) cnt[(k0[i].x / T) * TD + k0[i].y / T + 1]++;
+  for (int t = 0; t < c->ntiles; ++t) cnt[t + 1] += cnt[t];
+  {
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < M; ++i) perm[pos[(k0[i].x / T) * TD + k0[i].y / T]++] = (int)i;
+  }
+  // per-tile lists of sorted indices whose footprint meets the tile
+  std::vector<int> lcnt(c->ntiles + 1, 0);
+  auto tiles_of = [&](int64_t si, int* tl) {
+    const int2 k = k0[perm[si]];
+    const int r0 = k.x / T, r1 = ((k.x + J - 1) % L) / T;
+    const int c0 = k.y / T, c1 = ((k.y + J - 1) % L) / T;
+    int nt = 0;
+    const int rs[2] = {r0, r1}, cs[2] = {c0, c1};
+    for (int a = 0; a < (r1 != r0 ? 2 : 1); ++a)
+      for (int b = 0; b < (c1 != c0 ? 2 : 1); ++b) tl[nt++] = rs[a] * TD + cs[b];
+    return nt;
+  };
+  int tl[4];
+  for (int64_t si = 0; si < M; ++si) {
+    const int nt = tiles_of(si, tl);
+    for (int k = 0; k < nt; ++k) lcnt[tl[k] + 1]++;
+  }
+  for (int t = 0; t < c->ntiles; ++t) lcnt[t + 1] += lcnt[t];
+  c->nlist = lcnt[c->ntiles];
+  std::vector<int> list(c->nlist);
+  {
+    std::vector<int> pos(lcnt.begin(), lcnt.end() - 1);
+    for (int64_t si = 0; si < M; ++si) {
+      const int nt = tiles_of(si, tl);
+      for (int k = 0; k < nt; ++k) list[pos[tl[k]]++] = (int)si;
+    }
+  }
+  std::vector<int> order(c->ntiles);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return lcnt[a + 1] - lcnt[a] > lcnt[b + 1] - lcnt[b]; });
+  if ((st = dev_alloc(&c->d_uv, M)) == PURIFY_OK && (st = dev_alloc(&c->d_perm, M)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_off, c->ntiles + 1)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_list, c->nlist)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_order, c->ntiles)) == PURIFY_OK) {
+    cudaMemcpyAsync(c->d_perm, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_off, lcnt.data(), (c->ntiles + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_list, list.data(), c->nlist * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_order, order.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+    launch_gather_perm(M, d_uv_user, c->d_perm, c->d_uv, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
+  }
+  cudaFree(d_uv_user);
+  cudaFree(d_k0);
+  return st;
+}
+
+// One CG step on Q = Phi^H Phi + 2I (state in x, r, p; Qp into qp).
+int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* qp, cudaStream_t s) {
+  TRY(phi_forward_grid(c, kRowInCgDir, RowInArgs{r, p}, s));
+  DegridArgs da{};
+  da.out = c->d_vis;
+  TRY(degrid(c, kDegridSorted, da, s));
+  TRY(grid_adjoint(c, kGridSorted, c->d_vis, s));
+  RowOutArgs ra{};
+  ra.out = qp;
+  ra.p = p;
+  TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s));
+  return launch_cg_update(c, x, r, p, qp, s);
+}
+
+int64_t ctx_N(const purify_ctx* c) { return (int64_t)c->n * c->n; }
+int64_t ctx_D(const purify_ctx* c) { return (int64_t)c->q * c->n * c->n; }
+
+int load_data(purify_ctx* c, purify_sdmm_state* st, const float* y, cudaStream_t s) {
+  const int64_t M = c->M;
+  // caller order -> sorted order through the context's spare visibility buffer
+  TRY_CUDA(cudaMemcpyAsync(c->d_vis2, y, M * sizeof(float2), cudaMemcpyDefault, s));
+  TRY(launch_gather_perm(M, c->d_vis2, c->d_perm, st->y, s));
+  st->y_bf16 = 0;
+  return PURIFY_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* purify_status_string(int status) {
+  switch (status) {
+    case PURIFY_OK: return "ok";
+    case PURIFY_E_INVALID_ARG: return "invalid argument";
+    case PURIFY_E_SIZE: return "size out of the supported range";
+    case PURIFY_E_NOT_DEVICE_PTR: return "argument is not device memory";
+    case PURIFY_E_ALLOC: return "allocation failed";
+    case PURIFY_E_CUDA: return "CUDA runtime error";
+    case PURIFY_E_TIMEOUT: return "bounded device wait gave up";
+    case PURIFY_E_UNSUPPORTED: return "unsupported grid size";
+    default: return "unknown status";
+  }
+}
+
+int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purify_stream_t stream) {
+  if (!out) return PURIFY_E_INVALID_ARG;
+  *out = nullptr;
+  if (!d || !uv) return PURIFY_E_INVALID_ARG;
+  if (d->oversample != 2) return PURIFY_E_SIZE;
+  if (d->J != 2 && d->J != 4 && d->J != 6 && d->J != 8) return PURIFY_E_SIZE;
+  if (d->levels < 1 || d->levels > 6) return PURIFY_E_SIZE;
+  if (d->n < 8 || d->n > 2048 || d->n % (1 << d->levels) != 0 || d->n % 2 != 0) return PURIFY_E_SIZE;
+  if (d->M < 1 || d->M > 2147483647LL) return PURIFY_E_SIZE;
+  if (d->bases_mask == 0 || (d->bases_mask & ~0x1FFu)) return PURIFY_E_INVALID_ARG;
+  if (!good_side(2 * d->n)) return PURIFY_E_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  purify_ctx* c = new (std::nothrow) purify_ctx();
+  if (!c) return PURIFY_E_ALLOC;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PURIFY_E_CUDA; }
+  c->n = d->n;
+  c->L = 2 * d->n;
+  c->J = d->J;
+  c->levels = d->levels;
+  c->M = d->M;
+  c->mask = d->bases_mask;
+  c->q = 0;
+  for (int b = 0; b < 9; ++b)
+    if (c->mask & (1u << b)) c->bases[c->q++] = b;
+  c->kb = fit_kb(c->J);
+  const double sc = (double)c->L / (2.0 * M_PI);
+  c->ks.hi = (float)sc;
+  c->ks.lo = (float)(sc - (double)c->ks.hi);
+  c->plan = make_plan(c->L);
+  if (c->plan.nst < 0) { delete c; return PURIFY_E_UNSUPPORTED; }
+  make_daubechies(c->wf);
+  c->tileT = c->L >= 1024 ? 32 : (c->L >= 128 ? 16 : 8);
+  while (c->tileT < c->J || c->L % c->tileT) c->tileT *= 2;
+  c->tiles_1d = c->L / c->tileT;
+  c->ntiles = c->tiles_1d * c->tiles_1d;
+  const int64_t N = ctx_N(c), n2 = (int64_t)(c->n / 2) * (c->n / 2);
+  int st = PURIFY_OK;
+  auto fail = [&](int code) { free_ctx(c); return code; };
+  if ((st = dev_alloc(&c->d_deapod, c->n)) || (st = dev_alloc(&c->d_tw, c->L)) ||
+      (st = dev_alloc(&c->d_grid, (size_t)c->L * c->L)) || (st = dev_alloc(&c->d_half, (size_t)c->n * c->L)) ||
+      (st = dev_alloc(&c->d_vis, c->M)) || (st = dev_alloc(&c->d_vis2, c->M)) ||
+      (st = dev_alloc(&c->d_ll[0], c->q * n2)) || (st = dev_alloc(&c->d_ll[1], c->q * n2)) ||
+      (st = dev_alloc(&c->d_img[0], N)) || (st = dev_alloc(&c->d_img[1], N)) || (st = dev_alloc(&c->d_img[2], N)) ||
+      (st = dev_alloc(&c->d_img[3], N)) ||
+      (st = dev_alloc(&c->d_partials, (size_t)kNumCounters * 2 * kMaxPartials)) ||
+      (st = dev_alloc(&c->d_sc, 1)))
+    return fail(st);
+  if (cudaMallocHost((void**)&c->h_sc, sizeof(DevScalars)) != cudaSuccess) { cudaGetLastError(); return fail(PURIFY_E_ALLOC); }
+  // deapodisation 1 / g_hat((r - n/2) / 2n) and twiddles exp(-2 pi i m / L), in double
+  {
+    const double beta = kb_beta(c->J), i0b = std::cyl_bessel_i(0.0, beta);
+    std::vector<float> dz(c->n);
+    for (int r = 0; r < c->n; ++r) dz[r] = (float)(1.0 / kb_ghat((double)(r - c->n / 2) / c->L, c->J, beta, i0b));
+    std::vector<float2> tw(c->L);
+    for (int m = 0; m < c->L; ++m) {
+      const double a = -2.0 * M_PI * (double)m / c->L;
+      tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    if (cudaMemcpyAsync(c->d_deapod, dz.data(), c->n * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_tw, tw.data(), c->L * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_sc, 0, sizeof(DevScalars), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_ll[0], 0, c->q * n2 * sizeof(float2), s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_ll[1], 0, c->q * n2 * sizeof(float2), s) != cudaSuccess)
+      return fail(PURIFY_E_CUDA);
+    // dz and tw are pageable host vectors: finish the copies before they go out of scope
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PURIFY_E_CUDA);
+  }
+  if ((st = setup_visibilities(c, uv, s)) != PURIFY_OK) return fail(st);
+  // shared memory above 48 KB needs an opt-in per kernel; sizes here stay below it
+  *out = c;
+  return PURIFY_OK;
+}
+
+void purify_destroy(purify_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  free_ctx(c);
+}
+
+int purify_sizes(const purify_ctx* c, int64_t* N, int64_t* M, int32_t* q, int64_t* D) {
+  if (!c) return PURIFY_E_INVALID_ARG;
+  if (N) *N = ctx_N(c);
+  if (M) *M = c->M;
+  if (q) *q = c->q;
+  if (D) *D = ctx_D(c);
+  return PURIFY_OK;
+}
+
+int purify_phi(purify_ctx* c, const float* x, float* y, purify_stream_t stream) {
+  if (!c || !x || !y) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return PURIFY_E_NOT_DEVICE_PTR;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{(const float2*)x, nullptr}, s));
+  DegridArgs da{};
+  da.out = (float2*)y;
+  return degrid(c, kDegridPerm, da, s);
+}
+
+int purify_phi_adj(purify_ctx* c, const float* y, float* x, purify_stream_t stream) {
+  if (!c || !x || !y) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return PURIFY_E_NOT_DEVICE_PTR;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(grid_adjoint(c, kGridPerm, (const float2*)y, s));
+  RowOutArgs ra{};
+  ra.out = (float2*)x;
+  return phi_adjoint_image(c, kRowOutPlain, ra, s);
+}
+
+int purify_sara_analysis(purify_ctx* c, const float* x, float* alpha, purify_stream_t stream) {
+  if (!c || !x || !alpha) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(x) || !is_device_ptr(alpha)) return PURIFY_E_NOT_DEVICE_PTR;
+  SaraProxArgs pa{};
+  return sara_analysis(c, (const float2*)x, (float2*)alpha, kSaraPlain, pa, (cudaStream_t)stream);
+}
+
+int purify_sara_synthesis(purify_ctx* c, const float* alpha, float* x, purify_stream_t stream) {
+  if (!c || !x || !alpha) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(x) || !is_device_ptr(alpha)) return PURIFY_E_NOT_DEVICE_PTR;
+  return sara_synthesis(c, (const float2*)alpha, (float2*)x, (cudaStream_t)stream);
+}
+
+int purify_prox_l1_reweighted(purify_ctx* c, int64_t count, const float* in, const float* w, float gamma,
+                              float* out, purify_stream_t stream) {
+  if (!c || !in || !out || count < 0 || !(gamma >= 0.0f)) return PURIFY_E_INVALID_ARG;
+  if (count == 0) return PURIFY_OK;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(in) || !is_device_ptr(out) || (w && !is_device_ptr(w))) return PURIFY_E_NOT_DEVICE_PTR;
+  return launch_soft_threshold(count, (const float2*)in, w, nullptr, gamma, (float2*)out, (cudaStream_t)stream);
+}
+
+int purify_proj_l2ball(purify_ctx* c, int64_t count, const float* in, const float* y, double eps, float* out,
+                       double* norm_out, purify_stream_t stream) {
+  if (!c || !in || !y || !out || count < 0 || !(eps >= 0.0)) return PURIFY_E_INVALID_ARG;
+  if (count == 0) return PURIFY_OK;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(in) || !is_device_ptr(out) || !is_device_ptr(y) || (norm_out && !is_device_ptr(norm_out)))
+    return PURIFY_E_NOT_DEVICE_PTR;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(launch_l2_norm_diff(c, count, (const float2*)in, (const float2*)y, s));
+  TRY(launch_l2_project(count, (const float2*)in, (const float2*)y, eps, &c->d_sc->norm2, (float2*)out, s));
+  if (norm_out) {
+    k_sqrt_to<<<1, 1, 0, s>>>(&c->d_sc->norm2, norm_out);
+    TRY_CUDA(cudaGetLastError());
+  }
+  return PURIFY_OK;
+}
+
+int purify_proj_positive(purify_ctx* c, int64_t count, const float* in, float* out, purify_stream_t stream) {
+  if (!c || !in || !out || count < 0) return PURIFY_E_INVALID_ARG;
+  if (count == 0) return PURIFY_OK;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(in) || !is_device_ptr(out)) return PURIFY_E_NOT_DEVICE_PTR;
+  return launch_positive(count, (const float2*)in, (float2*)out, (cudaStream_t)stream);
+}
+
+int purify_cg_solve(purify_ctx* c, const float* b, float* x, int32_t iters, double* resid_out,
+                    purify_stream_t stream) {
+  if (!c || !b || !x || iters < 0) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(b) || !is_device_ptr(x) || (resid_out && !is_device_ptr(resid_out)))
+    return PURIFY_E_NOT_DEVICE_PTR;
+  cudaStream_t s = (cudaStream_t)stream;
+  float2* X = (float2*)x;
+  float2 *r = c->d_img[0], *p = c->d_img[1], *qp = c->d_img[2];
+  // Q x0 through the CG epilogue (p := x0), then r = b - Q x0, p = r
+  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{X, nullptr}, s));
+  DegridArgs da{};
+  da.out = c->d_vis;
+  TRY(degrid(c, kDegridSorted, da, s));
+  TRY(grid_adjoint(c, kGridSorted, c->d_vis, s));
+  RowOutArgs ra{};
+  ra.out = qp;
+  ra.p = X;
+  TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s));
+  TRY(launch_cg_residual_init(c, (const float2*)b, qp, r, p, s));
+  for (int k = 0; k < iters; ++k) TRY(cg_step(c, X, r, p, qp, s));
+  if (resid_out) TRY_CUDA(cudaMemcpyAsync(resid_out, &c->d_sc->cg_res, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return PURIFY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SDMM
+// ---------------------------------------------------------------------------
+void purify_sdmm_default_params(purify_sdmm_params* p) {
+  if (!p) return;
+  p->max_iters = 300;
+  p->cg_iters = 10;
+  p->rounds = 1;
+  p->check_every = 0;
+  p->beta = 1e-3;
+  p->xi = 1e-3;
+  p->tau = 0.1;
+}
+
+void purify_sdmm_state_destroy(purify_sdmm_state* st) {
+  if (!st) return;
+  DeviceGuard g(st->ctx->device);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->x1, st->z3, st->z1, st->u1,
+                  st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete st;
+}
+
+int purify_sdmm_state_create(purify_ctx* c, purify_sdmm_state** out) {
+  if (!c || !out) return PURIFY_E_INVALID_ARG;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  purify_sdmm_state* st = new (std::nothrow) purify_sdmm_state();
+  if (!st) return PURIFY_E_ALLOC;
+  st->ctx = c;
+  const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
+  int e;
+  if ((e = dev_alloc(&st->xhat, N)) || (e = dev_alloc(&st->r, N)) || (e = dev_alloc(&st->p, N)) ||
+      (e = dev_alloc(&st->qp, N)) || (e = dev_alloc(&st->x1, N)) || (e = dev_alloc(&st->z3, N)) ||
+      (e = dev_alloc(&st->z1, D)) || (e = dev_alloc(&st->u1, D)) || (e = dev_alloc(&st->w, D)) ||
+      (e = dev_alloc(&st->y, M)) || (e = dev_alloc(&st->yb, 2 * M)) || (e = dev_alloc(&st->yscale, (M + 4095) / 4096)) ||
+      (e = dev_alloc(&st->z2, M)) || (e = dev_alloc(&st->s2, M)) || (e = dev_alloc(&st->v, M))) {
+    purify_sdmm_state_destroy(st);
+    return e;
+  }
+  purify_sdmm_default_params(&st->params);
+  *out = st;
+  return PURIFY_OK;
+}
+
+int purify_sdmm_set_data(purify_ctx* c, purify_sdmm_state* st, const float* y, purify_stream_t stream) {
+  if (!c || !st || !y || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  return load_data(c, st, y, (cudaStream_t)stream);
+}
+
+int purify_sdmm_set_data_bf16(purify_ctx* c, purify_sdmm_state* st, const float* y, purify_stream_t stream) {
+  if (!c || !st || !y || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(load_data(c, st, y, s));
+  TRY(launch_quantize_bf16(c->M, st->y, st->yb, st->yscale, s));
+  st->y_bf16 = 1;
+  return PURIFY_OK;
+}
+
+int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, double eps,
+                     const purify_sdmm_params* params, purify_stream_t stream) {
+  if (!c || !st || !y || st->ctx != c || !(eps > 0.0)) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (params) st->params = *params;
+  if (st->params.cg_iters < 0 || st->params.max_iters < 0 || st->params.rounds < 1) return PURIFY_E_INVALID_ARG;
+  const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
+  TRY(load_data(c, st, y, s));
+  st->eps = eps;
+  st->iters = 0;
+  TRY_CUDA(cudaMemsetAsync(st->xhat, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->r, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->p, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->qp, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->x1, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->z3, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->z1, 0, D * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->u1, 0, D * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->z2, 0, M * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->s2, 0, M * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->v, 0, M * sizeof(float2), s));
+  k_fill_f32<<<nblk(D), 256, 0, s>>>(D, st->w, 1.0f);
+  TRY_CUDA(cudaGetLastError());
+  // scalars: everything zero but eps
+  DevScalars z{};
+  z.eps = eps;
+  std::memcpy(c->h_sc, &z, sizeof(z));
+  TRY_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+  // gamma = beta ||Psi^H Phi^H y||_inf (§4.4), via Phi^H y (sorted) into x1 and Psi^H into u1
+  TRY(grid_adjoint(c, kGridSorted, st->y, s));
+  RowOutArgs ra{};
+  ra.out = st->x1;
+  TRY(phi_adjoint_image(c, kRowOutPlain, ra, s));
+  SaraProxArgs pa{};
+  TRY(sara_analysis(c, st->x1, st->u1, kSaraPlain, pa, s));
+  TRY(launch_max_abs(c, D, st->u1, s));
+  TRY(launch_set_gamma(c, st->params.beta, s));
+  TRY_CUDA(cudaMemsetAsync(st->x1, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->u1, 0, D * sizeof(float2), s));
+  // the host staging copy of the scalars must land before h_sc is reused
+  TRY_CUDA(cudaStreamSynchronize(s));
+  return PURIFY_OK;
+}
+
+int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t stream) {
+  if (!c || !st || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r, p hold r0 = b - Q x_hat(t-1))
+  for (int k = 0; k < st->params.cg_iters; ++k) TRY(cg_step(c, st->xhat, st->r, st->p, st->qp, s));
+  // i = 2, first half: s2 = Phi x_hat and the l2 norms (FP64)
+  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{st->xhat, nullptr}, s));
+  DegridArgs da{};
+  da.out = st->s2;
+  da.z2 = st->z2;
+  da.y = st->y_bf16 ? nullptr : st->y;
+  da.yb = st->yb;
+  da.yscale = st->yscale;
+  TRY(degrid(c, kDegridSdmm, da, s));
+  // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
+  SaraProxArgs pa{st->z1, st->u1, st->w};
+  TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
+  // i = 2, second half: ball projection, z2 update, v = u2 - s2
+  TRY(launch_sdmm_l2_update(st, s));
+  // x1 = Psi u1
+  TRY(sara_synthesis(c, st->u1, st->x1, s));
+  // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual
+  TRY(grid_adjoint(c, kGridSorted, st->v, s));
+  RowOutArgs ra{};
+  ra.out = st->r;
+  ra.p = st->xhat;
+  ra.x1 = st->x1;
+  ra.z3 = st->z3;
+  ra.pdir = st->p;
+  TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s));
+  st->iters++;
+  return PURIFY_OK;
+}
+
+int purify_sdmm_reweight(purify_ctx* c, purify_sdmm_state* st, int32_t round, purify_stream_t stream) {
+  if (!c || !st || st->ctx != c || round < 1) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t D = ctx_D(c);
+  SaraProxArgs pa{};
+  TRY(sara_analysis(c, st->xhat, st->u1, kSaraPlain, pa, s));
+  TRY(launch_max_abs(c, D, st->u1, s));
+  return launch_reweight(c, D, st->u1, st->w, round, s);
+}
+
+int purify_sdmm_set_weights(purify_ctx* c, purify_sdmm_state* st, const float* w, purify_stream_t stream) {
+  if (!c || !st || !w || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(w)) return PURIFY_E_NOT_DEVICE_PTR;
+  return check_cuda(cudaMemcpyAsync(st->w, w, ctx_D(c) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream));
+}
+
+int purify_sdmm_get_image(purify_ctx* c, purify_sdmm_state* st, float* x_out, purify_stream_t stream) {
+  if (!c || !st || !x_out || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY_CUDA(cudaMemcpyAsync(x_out, st->xhat, ctx_N(c) * sizeof(float2), cudaMemcpyDefault, s));
+  if (!is_device_ptr(x_out)) TRY_CUDA(cudaStreamSynchronize(s));
+  return PURIFY_OK;
+}
+
+int purify_sdmm_get_report(purify_ctx* c, purify_sdmm_state* st, purify_report* rep, purify_stream_t stream) {
+  if (!c || !st || !rep || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  TRY_CUDA(cudaStreamSynchronize(s));
+  rep->iters = st->iters;
+  rep->f1 = c->h_sc->f1;
+  rep->zeta = c->h_sc->zeta;
+  rep->nu = c->h_sc->nu;
+  rep->gamma = c->h_sc->gamma;
+  rep->cg_residual = c->h_sc->cg_res;
+  return PURIFY_OK;
+}
+
+int purify_sdmm_solve(purify_ctx* c, const float* y, double eps, const purify_sdmm_params* params, float* x_out,
+                      purify_report* report, purify_stream_t stream) {
+  if (!c || !y || !x_out || !(eps > 0.0)) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  purify_sdmm_state* st = nullptr;
+  TRY(purify_sdmm_state_create(c, &st));
+  int rc = purify_sdmm_init(c, st, y, eps, params, stream);
+  purify_report rep{};
+  for (int round = 0; rc == PURIFY_OK && round < st->params.rounds; ++round) {
+    if (round > 0) rc = purify_sdmm_reweight(c, st, round, stream);
+    for (int it = 0; rc == PURIFY_OK && it < st->params.max_iters; ++it) {
+      rc = purify_sdmm_step(c, st, stream);
+      if (rc == PURIFY_OK && st->params.check_every > 0 && (it + 1) % st->params.check_every == 0) {
+        rc = purify_sdmm_get_report(c, st, &rep, stream);
+        if (rc == PURIFY_OK && rep.zeta < st->params.xi && rep.nu >= 1.0 - st->params.tau &&
+            rep.nu <= 1.0 + st->params.tau)
+          break;
+      }
+    }
+  }
+  if (rc == PURIFY_OK) rc = purify_sdmm_get_image(c, st, x_out, stream);
+  if (rc == PURIFY_OK && report) rc = purify_sdmm_get_report(c, st, report, stream);
+  if (rc == PURIFY_OK) rc = check_cuda(cudaStreamSynchronize((cudaStream_t)stream));
+  purify_sdmm_state_destroy(st);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint blob: header, then xhat r p x1 z3 (N each), z1 (D), w (D float),
+// z2 (M), y (M), then the device scalars.
+// ---------------------------------------------------------------------------
+struct BlobHeader {
+  uint64_t magic;
+  int64_t n, M, q, iters;
+  double eps;
+};
+static const uint64_t kBlobMagic = 0x5055524946594331ull;  // "PURIFYC1"
+
+static size_t blob_bytes(const purify_ctx* c) {
+  const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
+  return sizeof(BlobHeader) + (5 * N + D + 2 * M) * sizeof(float2) + D * sizeof(float) + sizeof(DevScalars);
+}
+
+int purify_sdmm_state_bytes(purify_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return PURIFY_E_INVALID_ARG;
+  *bytes = blob_bytes(c);
+  return PURIFY_OK;
+}
+
+int purify_sdmm_export(purify_ctx* c, purify_sdmm_state* st, void* host_buf, size_t bytes, purify_stream_t stream) {
+  if (!c || !st || !host_buf || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  if (bytes < blob_bytes(c)) return PURIFY_E_SIZE;
+  if (st->y_bf16) return PURIFY_E_UNSUPPORTED;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
+  char* p = (char*)host_buf;
+  BlobHeader h{kBlobMagic, c->n, c->M, c->q, st->iters, st->eps};
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  float2* vecs[] = {st->xhat, st->r, st->p, st->x1, st->z3};
+  for (float2* v : vecs) {
+    TRY_CUDA(cudaMemcpyAsync(p, v, N * sizeof(float2), cudaMemcpyDeviceToHost, s));
+    p += N * sizeof(float2);
+  }
+  TRY_CUDA(cudaMemcpyAsync(p, st->z1, D * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  p += D * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(p, st->w, D * sizeof(float), cudaMemcpyDeviceToHost, s));
+  p += D * sizeof(float);
+  TRY_CUDA(cudaMemcpyAsync(p, st->z2, M * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  p += M * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(p, st->y, M * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  p += M * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(p, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  return check_cuda(cudaStreamSynchronize(s));
+}
+
+int purify_sdmm_import(purify_ctx* c, purify_sdmm_state* st, const void* host_buf, size_t bytes,
+                       purify_stream_t stream) {
+  if (!c || !st || !host_buf || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  if (bytes < blob_bytes(c)) return PURIFY_E_SIZE;
+  const char* p = (const char*)host_buf;
+  BlobHeader h;
+  std::memcpy(&h, p, sizeof(h));
+  if (h.magic != kBlobMagic || h.n != c->n || h.M != c->M || h.q != c->q) return PURIFY_E_INVALID_ARG;
+  p += sizeof(h);
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
+  float2* vecs[] = {st->xhat, st->r, st->p, st->x1, st->z3};
+  for (float2* v : vecs) {
+    TRY_CUDA(cudaMemcpyAsync(v, p, N * sizeof(float2), cudaMemcpyHostToDevice, s));
+    p += N * sizeof(float2);
+  }
+  TRY_CUDA(cudaMemcpyAsync(st->z1, p, D * sizeof(float2), cudaMemcpyHostToDevice, s));
+  p += D * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(st->w, p, D * sizeof(float), cudaMemcpyHostToDevice, s));
+  p += D * sizeof(float);
+  TRY_CUDA(cudaMemcpyAsync(st->z2, p, M * sizeof(float2), cudaMemcpyHostToDevice, s));
+  p += M * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(st->y, p, M * sizeof(float2), cudaMemcpyHostToDevice, s));
+  p += M * sizeof(float2);
+  TRY_CUDA(cudaMemcpyAsync(c->d_sc, p, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+  st->iters = h.iters;
+  st->eps = h.eps;
+  st->y_bf16 = 0;
+  return check_cuda(cudaStreamSynchronize(s));
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Internal declarations of the sm_103a SDMM-SARA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "purify.h"
+
+namespace purify {
+
+// ---------------------------------------------------------------------------
+// Small complex helpers (float2 = complex64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// ---------------------------------------------------------------------------
+// Kaiser-Bessel kernel as per-tap polynomials.
+//
+// For a visibility with fractional offset x = kappa - floor(kappa) in [0, 1),
+// tap a (cell floor(kappa) - J/2 + 1 + a) has weight g(x + J/2 - 1 - a).  On
+// x in [0, 1) that is a smooth function; the host fits it, per tap, by a
+// polynomial in z = 2x - 1 (Chebyshev interpolation in double, converted to
+// monomials) so the device evaluates J weights by Horner.
+// ---------------------------------------------------------------------------
+constexpr int kMaxJ = 8;
+constexpr int kMaxKbDeg = 15;
+struct KbPoly {
+  int J;
+  int deg;                         // polynomial degree (<= kMaxKbDeg)
+  float c[kMaxJ][kMaxKbDeg + 1];   // c[a][k]: coefficient of z^k for tap a
+  float max_err;                   // max abs fit error measured on the host
+};
+
+// Error-free splitting of kappa = u * (2n / (2 pi)) into floor and fraction
+// with float arithmetic: scale = s_hi + s_lo (double-float), the product
+// error is recovered exactly with an FMA.
+struct KappaScale {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void split_kappa(float u, KappaScale s, int& k, float& frac) {
+  float p = u * s.hi;
+  float e = fmaf(u, s.hi, -p) + u * s.lo;  // exact product error + low part
+  float fl = floorf(p);
+  float f = (p - fl) + e;                  // p - fl is exact
+  if (f < 0.0f) { f += 1.0f; fl -= 1.0f; }
+  else if (f >= 1.0f) { f -= 1.0f; fl += 1.0f; }
+  k = (int)fl;
+  frac = f;
+}
+
+// Weights w[a], a = 0..J-1, for fractional offset x in [0, 1).
+template <int J>
+__device__ __forceinline__ void kb_weights(const KbPoly& kb, float x, float* w) {
+  const float z = fmaf(2.0f, x, -1.0f);
+#pragma unroll
+  for (int a = 0; a < J; ++a) {
+    float acc = kb.c[a][kb.deg];
+    for (int k = kb.deg - 1; k >= 0; --k) acc = fmaf(acc, z, kb.c[a][k]);
+    w[a] = acc;
+  }
+}
+
+__device__ __forceinline__ int wrap(int k, int L) {
+  k %= L;
+  return k < 0 ? k + L : k;
+}
+
+// ---------------------------------------------------------------------------
+// FFT plan: Stockham stages with radices in {2, 3, 4, 8}.
+// ---------------------------------------------------------------------------
+struct FftPlan {
+  int L;
+  int nst;
+  int radix[24];
+};
+
+// ---------------------------------------------------------------------------
+// Daubechies filters (db1..db8), generated on the host at library load.
+// h of db_p starts at off[p] and has 2p taps; the high-pass is derived.
+// ---------------------------------------------------------------------------
+struct WaveletFilters {
+  float h[72];
+  int off[9];
+};
+
+// ---------------------------------------------------------------------------
+// Device scalars of the reductions (FP64) and the SDMM bookkeeping.
+// ---------------------------------------------------------------------------
+enum CounterSlot {
+  kCntDot = 0,     // <p, Qp>
+  kCntRho,         // ||r||^2
+  kCntL2,          // ||s2 + z2 - y||^2 and ||s2 - y||^2
+  kCntF1,          // sum w |alpha|
+  kCntMax,         // max |.|
+  kCntNorm,        // generic ||a - b||^2
+  kCntRho0,        // ||r0||^2 after an SDMM step
+  kNumCounters
+};
+
+struct DevScalars {
+  double rho;        // current <r, r>
+  double alpha;      // CG step
+  double beta;       // CG direction update
+  double pqp;        // <p, Qp>
+  double l2_dn2;     // ||s2 + z2 - y||^2
+  double l2_res2;    // ||s2 - y||^2
+  double f1;         // sum w |Psi^H x|
+  double f1_prev;
+  double amax;       // max |.| reductions
+  double norm2;      // generic squared norm
+  double gamma;      // penalty
+  double eps;        // l2 bound
+  double zeta, nu;   // halting quantities
+  double iters;
+  double cg_res;
+  unsigned int counter[kNumCounters];
+};
+
+constexpr int kMaxPartials = 32768;  // blocks per reduction (NV <= 2 values each)
+
+}  // namespace purify
+
+// ---------------------------------------------------------------------------
+// The context (opaque to callers).
+// ---------------------------------------------------------------------------
+struct purify_ctx {
+  int device;
+  int n, L, J, levels, q;
+  int64_t M;
+  uint32_t mask;
+  int bases[9];  // basis index (0 = Dirac, p = db_p) of each plane
+
+  purify::KbPoly kb;
+  purify::KappaScale ks;
+  purify::FftPlan plan;
+  purify::WaveletFilters wf;
+
+  float* d_deapod;      // n: 1 / g_hat((r - n/2) / 2n)
+  float2* d_tw;         // L: exp(-2 pi i m / L)
+
+  // visibility table (sorted by grid tile of the first footprint cell)
+  float2* d_uv;         // M sorted frequencies
+  int* d_perm;          // sorted position -> caller position
+  int tileT;            // tile side (cells)
+  int tiles_1d;         // L / tileT
+  int ntiles;
+  int* d_tile_off;      // ntiles + 1 offsets into d_tile_list
+  int* d_tile_list;     // sorted visibility indices whose footprint meets the tile
+  int* d_tile_order;    // tiles by decreasing list length
+  int64_t nlist;
+
+  // scratch
+  float2* d_grid;       // L x L
+  float2* d_half;       // n x L (rows of the image after the row pass)
+  float2* d_vis;        // M (sorted order)
+  float2* d_vis2;       // M
+  float2* d_ll[2];      // q x (n/2)^2 each: low-low ping-pong of the DWT
+  float2* d_img[4];     // N each: CG work vectors of purify_cg_solve
+  double* d_partials;   // kNumCounters x kMaxPartials
+  purify::DevScalars* d_sc;
+  purify::DevScalars* h_sc;  // pinned host mirror
+};
+
+struct purify_sdmm_state {
+  purify_ctx* ctx;
+  // image-size vectors
+  float2* xhat;   // N
+  float2* r;      // N  CG residual
+  float2* p;      // N  CG direction
+  float2* qp;     // N  Q p
+  float2* x1;     // N  Psi u1
+  float2* z3;     // N
+  // coefficient-size vectors
+  float2* z1;     // D
+  float2* u1;     // D
+  float* w;       // D weights
+  // visibility-size vectors (sorted order)
+  float2* y;      // M data
+  uint16_t* yb;   // 2M bf16 data (when bf16)
+  float* yscale;  // ceil(M/4096)
+  int y_bf16;
+  float2* z2;     // M
+  float2* s2;     // M   Phi x_hat
+  float2* v;      // M   u2 - Phi x_hat
+  double eps;
+  int64_t iters;
+  purify_sdmm_params params;
+};
+
+namespace purify {
+
+// Launchers (implemented in the .cu files).
+int check_cuda(cudaError_t e);
+
+// nufft.cu
+enum RowInMode { kRowInPlain = 0, kRowInCgDir = 1 };
+enum DegridOut { kDegridPerm = 0, kDegridSorted = 1, kDegridSdmm = 2 };
+enum GridIn { kGridPerm = 0, kGridSorted = 1 };
+enum RowOutMode { kRowOutPlain = 0, kRowOutCgQ = 1, kRowOutSdmm = 2 };
+
+struct RowInArgs {
+  const float2* x;      // image (plain) or r (cg)
+  float2* p;            // cg: direction, updated in place to r + beta p
+};
+struct DegridArgs {
+  float2* out;              // y (perm) or sorted output
+  const float2* z2;         // sdmm
+  const float2* y;          // sdmm data (sorted) or NULL when bf16
+  const uint16_t* yb;       // sdmm bf16 data
+  const float* yscale;
+};
+struct RowOutArgs {
+  float2* out;          // plain: image; cg: Qp; sdmm: r0
+  const float2* p;      // cg: p; sdmm: x_hat
+  const float2* x1;     // sdmm: Psi u1
+  float2* z3;           // sdmm
+  float2* pdir;         // sdmm: p0 = r0
+};
+
+int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s);
+int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s);
+int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s);
+int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s);
+
+// sara.cu
+enum SaraMode { kSaraPlain = 0, kSaraProx = 1 };
+struct SaraProxArgs {
+  float2* z1;
+  float2* u1;
+  const float* w;       // NULL = 1
+};
+int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode,
+                  const SaraProxArgs& pa, cudaStream_t s);
+int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s);
+void make_daubechies(WaveletFilters& wf);
+
+// vecops.cu
+int launch_soft_threshold(int64_t count, const float2* in, const float* w, const double* gamma_dev,
+                          float gamma, float2* out, cudaStream_t s);
+int launch_l2_norm_diff(purify_ctx* c, int64_t count, const float2* a, const float2* b, cudaStream_t s);
+int launch_l2_project(int64_t count, const float2* in, const float2* y, double eps,
+                      const double* norm2_dev, float2* out, cudaStream_t s);
+int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s);
+int launch_cg_update(purify_ctx* c, float2* x, float2* r, const float2* p, const float2* qp,
+                     cudaStream_t s);
+int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, float2* p,
+                            cudaStream_t s);
+int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s);
+int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s);
+int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round,
+                    cudaStream_t s);
+int launch_quantize_bf16(int64_t M, const float2* y, uint16_t* yb, float* yscale, cudaStream_t s);
+int launch_gather_perm(int64_t M, const float2* src, const int* perm, float2* dst, cudaStream_t s);
+int launch_set_gamma(purify_ctx* c, double beta, cudaStream_t s);
+
+}  // namespace purify

@@ -1,0 +1,144 @@
+// Shared-memory Stockham FFT building blocks (forward sign; inverse by conjugation).
+//
+// The unitary DFT F of §5 eq. opmodel, X[k] = (1/L) sum_j g[j] exp(-2 pi i k.j / L)
+// per axis pair, is computed as 1-D transforms of rows and of columns.  One CTA
+// holds `nsig` signals of length L in shared memory and runs the Stockham
+// autosort stages on them: stage (radix R, Ns = product of earlier radices)
+// reads R values spaced L/R apart, twiddles them by exp(-2 pi i r k / (Ns R)),
+// k = j mod Ns, does a radix-R DFT and writes them Ns apart from
+// (j / Ns) Ns R + k.  The output is in natural order.
+#pragma once
+
+#include "common.cuh"
+
+namespace purify {
+
+template <int R>
+__device__ __forceinline__ void dft_small(float2* v);
+
+template <>
+__device__ __forceinline__ void dft_small<2>(float2* v) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+// -i * a
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+template <>
+__device__ __forceinline__ void dft_small<4>(float2* v) {
+  float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+  float2 a2 = cadd(v[1], v[3]), a3 = mul_mi(csub(v[1], v[3]));
+  v[0] = cadd(a0, a2);
+  v[2] = csub(a0, a2);
+  v[1] = cadd(a1, a3);
+  v[3] = csub(a1, a3);
+}
+
+template <>
+__device__ __forceinline__ void dft_small<3>(float2* v) {
+  const float h = 0.8660254037844386f;  // sqrt(3)/2
+  float2 s = cadd(v[1], v[2]);
+  float2 d = csub(v[1], v[2]);
+  float2 t = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+  float2 m = make_float2(h * d.y, -h * d.x);  // -i sqrt(3)/2 d
+  v[0] = cadd(v[0], s);
+  v[1] = cadd(t, m);
+  v[2] = csub(t, m);
+}
+
+template <>
+__device__ __forceinline__ void dft_small<8>(float2* v) {
+  const float r = 0.70710678118654752f;
+  // radix-4 on evens and odds, then combine with exp(-2 pi i k / 8)
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft_small<4>(e);
+  dft_small<4>(o);
+  float2 o1 = make_float2(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));   // * (1 - i)/sqrt2
+  float2 o2 = mul_mi(o[2]);                                               // * -i
+  float2 o3 = make_float2(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));  // * (-1 - i)/sqrt2
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+// Shared-memory address of element e of signal s.
+struct SigLayout {
+  int sstride;  // between signals
+  int estride;  // between elements of one signal
+  __device__ __forceinline__ int at(int s, int e) const { return s * sstride + e * estride; }
+};
+
+// One Stockham stage over all signals held by the CTA.  Each thread owns
+// EPT / R butterflies; butterfly b maps to (signal, j) either signal-fastest
+// (SIG_FAST, for column transforms where signals are adjacent in memory) or
+// element-fastest.  nsig * L == blockDim.x * EPT.
+template <int R, int EPT, bool SIG_FAST>
+__device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L, int Ns, int nsig,
+                                               const float2* __restrict__ tw) {
+  static_assert(EPT % R == 0, "radix must divide elements per thread");
+  constexpr int NB = EPT / R;
+  const int nthr = blockDim.x;
+  const int LR = L / R;
+  const int twstep = L / (Ns * R);
+  float2 v[EPT];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * nthr;
+    int s, j;
+    if (SIG_FAST) { s = b % nsig; j = b / nsig; }
+    else { j = b % LR; s = b / LR; }
+    const int kk = j % Ns;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[k * R + r] = buf[lay.at(s, j + r * LR)];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], __ldg(&tw[r * kk * twstep]));
+    }
+    dft_small<R>(&v[k * R]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * nthr;
+    int s, j;
+    if (SIG_FAST) { s = b % nsig; j = b / nsig; }
+    else { j = b % LR; s = b / LR; }
+    const int kk = j % Ns;
+    const int base = (j / Ns) * Ns * R + kk;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[lay.at(s, base + r * Ns)] = v[k * R + r];
+  }
+  __syncthreads();
+}
+
+// Forward FFT of all signals in shared memory (in place, natural order).
+template <int EPT, bool SIG_FAST>
+__device__ __forceinline__ void fft_smem(float2* buf, SigLayout lay, const FftPlan& plan, int nsig,
+                                         const float2* __restrict__ tw) {
+  int Ns = 1;
+  for (int st = 0; st < plan.nst; ++st) {
+    const int R = plan.radix[st];
+    if constexpr (EPT % 8 == 0) {
+      if (R == 8) { stockham_stage<8, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 8; continue; }
+    }
+    if constexpr (EPT % 4 == 0) {
+      if (R == 4) { stockham_stage<4, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 4; continue; }
+    }
+    if constexpr (EPT % 3 == 0) {
+      if (R == 3) { stockham_stage<3, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 3; continue; }
+    }
+    if constexpr (EPT % 2 == 0) {
+      if (R == 2) { stockham_stage<2, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 2; continue; }
+    }
+  }
+}
+
+}  // namespace purify

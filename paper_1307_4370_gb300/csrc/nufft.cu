@@ -1,0 +1,451 @@
+// Measurement operator Phi = G F D Z (§5 eq. opmodel, B = I) and its adjoint.
+//
+// Forward:  k_row_fwd   D Z and the row DFTs of the n non-zero grid rows
+//                       (the zero padding is never written);
+//           k_col_fwd   column DFTs, reading only the n non-zero rows;
+//           k_degrid    G: Kaiser-Bessel gather of J x J cells per visibility.
+// Adjoint:  k_grid      G^T: per grid tile, shared-memory accumulation of the
+//                       visibilities whose footprint meets the tile (no global
+//                       atomics; each tile is written once);
+//           k_col_inv   inverse column DFTs, keeping the n rows of the image;
+//           k_row_inv   inverse row DFTs, crop Z^T and D, with fused epilogues
+//                       for the CG operator Q = Phi^H Phi + 2I and the SDMM step.
+#include "common.cuh"
+#include "fft.cuh"
+#include "reduce.cuh"
+
+namespace purify {
+
+// ---------------------------------------------------------------------------
+// Launch shapes
+// ---------------------------------------------------------------------------
+struct FftShape {
+  int ept;      // elements per thread (8, 12 or 16)
+  int nsig;     // signals per CTA
+  int threads;  // nsig * L / ept
+};
+
+static int pick_ept(int L) { return (L % 3 == 0) ? 12 : 8; }
+
+// Row passes: nsig rows per CTA, about 256 threads, nsig divides n.
+static FftShape row_shape(const purify_ctx* c) {
+  FftShape f;
+  f.ept = pick_ept(c->L);
+  int nsig = 1;
+  while (nsig * 2 * c->L / f.ept <= 256 && c->n % (nsig * 2) == 0) nsig *= 2;
+  f.nsig = nsig;
+  f.threads = nsig * c->L / f.ept;
+  return f;
+}
+
+// Column passes: nsig adjacent columns per CTA (>= 4 for 32-byte segments).
+static FftShape col_shape(const purify_ctx* c) {
+  FftShape f;
+  f.ept = pick_ept(c->L);
+  int nsig = 4;
+  while (nsig * 2 * c->L / f.ept <= 256 && c->L % (nsig * 2) == 0 && nsig < 16) nsig *= 2;
+  while (nsig > 1 && nsig * c->L / f.ept > 1024) nsig /= 2;  // at most 1024 threads
+  f.nsig = nsig;
+  f.threads = nsig * c->L / f.ept;
+  return f;
+}
+
+// Dynamic shared memory above 48 KB needs a per-kernel opt-in.
+template <class K>
+static void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// Forward row pass: g[r][e] = x[r][c] / (ghat_r ghat_c) / L at e = (c - n/2) mod L,
+// then the row DFT; rows stored in `half` (n x L).
+// ---------------------------------------------------------------------------
+template <int EPT, int MODE>
+__global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
+                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
+                          const DevScalars* __restrict__ sc) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int r0 = blockIdx.x * nsig;
+  const float invL = 1.0f / (float)L;
+  float beta = 0.0f;
+  if (MODE == kRowInCgDir) beta = (float)sc->beta;
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int s = idx / L, e = idx - s * L;
+    const int r = r0 + s;
+    int cc = e + (n >> 1);
+    if (cc >= L) cc -= L;
+    float2 v = make_float2(0.f, 0.f);
+    if (cc < n) {
+      const size_t off = (size_t)r * n + cc;
+      if (MODE == kRowInCgDir) {
+        float2 rr = a.x[off], pp = a.p[off];
+        v = make_float2(fmaf(beta, pp.x, rr.x), fmaf(beta, pp.y, rr.y));
+        a.p[off] = v;
+      } else {
+        v = a.x[off];
+      }
+      const float f = dz[r] * dz[cc] * invL;
+      v = cscale(v, f);
+    }
+    sm[s * L + e] = v;
+  }
+  __syncthreads();
+  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tw);
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int s = idx / L, e = idx - s * L;
+    half[(size_t)(r0 + s) * L + e] = sm[s * L + e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward column pass: column c of the grid holds half[r][c] at row
+// (r - n/2) mod L and zeros elsewhere; DFT along the column into X.
+// ---------------------------------------------------------------------------
+template <int EPT>
+__global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ half, float2* __restrict__ X,
+                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int c0 = blockIdx.x * nsig;
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int e = idx / nsig, s = idx - e * nsig;
+    int r = e + (n >> 1);
+    if (r >= L) r -= L;
+    sm[e * nsig + s] = (r < n) ? half[(size_t)r * L + c0 + s] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tw);
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int e = idx / nsig, s = idx - e * nsig;
+    X[(size_t)e * L + c0 + s] = sm[e * nsig + s];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Degridding G: one thread per (sorted) visibility.
+// ---------------------------------------------------------------------------
+template <int J, int MODE>
+__global__ void k_degrid(const float2* __restrict__ X, const float2* __restrict__ uv,
+                         const int* __restrict__ perm, DegridArgs a, KbPoly kb, KappaScale ks,
+                         int L, int64_t M, double* partials, DevScalars* sc) {
+  double acc2[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 u = __ldg(&uv[i]);
+    int k0r, k0c;
+    float fr, fc;
+    split_kappa(u.x, ks, k0r, fr);
+    split_kappa(u.y, ks, k0c, fc);
+    k0r -= J / 2 - 1;
+    k0c -= J / 2 - 1;
+    float wr[J], wc[J];
+    kb_weights<J>(kb, fr, wr);
+    kb_weights<J>(kb, fc, wc);
+    int col[J];
+#pragma unroll
+    for (int b = 0; b < J; ++b) col[b] = wrap(k0c + b, L);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int aa = 0; aa < J; ++aa) {
+      const float2* row = X + (size_t)wrap(k0r + aa, L) * L;
+      float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int b = 0; b < J; ++b) {
+        const float2 g = __ldg(&row[col[b]]);
+        t.x = fmaf(wc[b], g.x, t.x);
+        t.y = fmaf(wc[b], g.y, t.y);
+      }
+      acc.x = fmaf(wr[aa], t.x, acc.x);
+      acc.y = fmaf(wr[aa], t.y, acc.y);
+    }
+    if (MODE == kDegridPerm) {
+      a.out[perm[i]] = acc;
+    } else if (MODE == kDegridSorted) {
+      a.out[i] = acc;
+    } else {
+      // SDMM: s2 = Phi x_hat, and the two FP64 norms of the l2 branch
+      a.out[i] = acc;
+      float2 y;
+      if (a.y) {
+        y = a.y[i];
+      } else {
+        const float sc4 = a.yscale[i >> 12];
+        const uint32_t bits = reinterpret_cast<const uint32_t*>(a.yb)[i];
+        y = make_float2(__uint_as_float(bits << 16) * sc4, __uint_as_float(bits & 0xffff0000u) * sc4);
+      }
+      const float2 z = a.z2[i];
+      const double dx = (double)acc.x + (double)z.x - (double)y.x;
+      const double dy = (double)acc.y + (double)z.y - (double)y.y;
+      const double ex = (double)acc.x - (double)y.x;
+      const double ey = (double)acc.y - (double)y.y;
+      acc2[0] += dx * dx + dy * dy;
+      acc2[1] += ex * ex + ey * ey;
+    }
+  }
+  if (MODE == kDegridSdmm) {
+    double tot[2];
+    if (reduce_last_block<2>(acc2, partials + kCntL2 * 2 * kMaxPartials, &sc->counter[kCntL2], tot)) {
+      sc->l2_dn2 = tot[0];
+      sc->l2_res2 = tot[1];
+      sc->nu = sqrt(tot[1]) / sc->eps;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gridding G^T: one CTA per output tile (T x T cells), in decreasing order of
+// work.  Visibilities whose footprint meets the tile are listed at set-up;
+// their contributions to cells inside the tile are summed in shared memory,
+// and the tile is written to X once.
+// ---------------------------------------------------------------------------
+template <int J, int MODE>
+__global__ void k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
+                       const int* __restrict__ perm, const float2* __restrict__ vis,
+                       const int* __restrict__ tile_off, const int* __restrict__ tile_list,
+                       const int* __restrict__ tile_order, KbPoly kb, KappaScale ks, int L, int T,
+                       int tiles_1d) {
+  extern __shared__ float smf[];
+  float* accr = smf;
+  float* acci = smf + T * T;
+  const int tile = tile_order[blockIdx.x];
+  const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
+  const int R0 = tr * T, C0 = tc * T;
+  for (int k = threadIdx.x; k < T * T; k += blockDim.x) { accr[k] = 0.f; acci[k] = 0.f; }
+  __syncthreads();
+  const int beg = tile_off[tile], end = tile_off[tile + 1];
+  for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int i = tile_list[e];
+    const float2 u = __ldg(&uv[i]);
+    const float2 val = (MODE == kGridPerm) ? __ldg(&vis[perm[i]]) : __ldg(&vis[i]);
+    int k0r, k0c;
+    float fr, fc;
+    split_kappa(u.x, ks, k0r, fr);
+    split_kappa(u.y, ks, k0c, fc);
+    k0r -= J / 2 - 1;
+    k0c -= J / 2 - 1;
+    float wr[J], wc[J];
+    kb_weights<J>(kb, fr, wr);
+    kb_weights<J>(kb, fc, wc);
+    // offsets of the footprint relative to the tile origin (wrapped)
+    const int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
+#pragma unroll
+    for (int aa = 0; aa < J; ++aa) {
+      int rr = dr + aa;
+      if (rr >= L) rr -= L;
+      if (rr >= T) continue;
+      const float vr = wr[aa];
+#pragma unroll
+      for (int b = 0; b < J; ++b) {
+        int cc = dc + b;
+        if (cc >= L) cc -= L;
+        if (cc >= T) continue;
+        const float w = vr * wc[b];
+        atomicAdd(&accr[rr * T + cc], w * val.x);
+        atomicAdd(&acci[rr * T + cc], w * val.y);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+    const int rr = k / T, cc = k - rr * T;
+    X[(size_t)(R0 + rr) * L + C0 + cc] = make_float2(accr[k], acci[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse column pass: inverse DFT of columns of X, keep rows (r - n/2) mod L.
+// ---------------------------------------------------------------------------
+template <int EPT>
+__global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, float2* __restrict__ half,
+                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int c0 = blockIdx.x * nsig;
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int e = idx / nsig, s = idx - e * nsig;
+    sm[e * nsig + s] = cconj(X[(size_t)e * L + c0 + s]);
+  }
+  __syncthreads();
+  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tw);
+  for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
+    const int r = idx / nsig, s = idx - r * nsig;
+    int e = r - (n >> 1);
+    if (e < 0) e += L;
+    half[(size_t)r * L + c0 + s] = cconj(sm[e * nsig + s]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse row pass, crop and deapodise, with epilogues:
+//   plain: out = Phi^H (.)
+//   CG:    out = Qp = Phi^H Phi p + 2p, and <p, Qp> (FP64) -> alpha = rho / <p,Qp>
+//   SDMM:  positivity branch (z3, u3) and the warm-start CG residual
+//          r0 = x1 + u3 - 2 x_hat + Phi^H v; p = r0; rho = ||r0||^2
+// ---------------------------------------------------------------------------
+template <int EPT, int MODE>
+__global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ half, RowOutArgs a, const float* __restrict__ dz,
+                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
+                          double* partials, DevScalars* sc) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int r0 = blockIdx.x * nsig;
+  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
+    const int s = idx / L, e = idx - s * L;
+    sm[s * L + e] = cconj(half[(size_t)(r0 + s) * L + e]);
+  }
+  __syncthreads();
+  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tw);
+  const float invL = 1.0f / (float)L;
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
+    const int s = idx / n, c = idx - s * n;
+    const int r = r0 + s;
+    int e = c - (n >> 1);
+    if (e < 0) e += L;
+    const float f = dz[r] * dz[c] * invL;
+    const float2 v = cscale(cconj(sm[s * L + e]), f);
+    const size_t off = (size_t)r * n + c;
+    if (MODE == kRowOutPlain) {
+      a.out[off] = v;
+    } else if (MODE == kRowOutCgQ) {
+      const float2 p = a.p[off];
+      const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
+      a.out[off] = q;
+      acc += (double)p.x * (double)q.x + (double)p.y * (double)q.y;  // Re <p, Qp>
+    } else {
+      const float2 xh = a.p[off];
+      const float2 z3 = a.z3[off];
+      const float2 a3 = cadd(xh, z3);
+      const float r3 = fmaxf(a3.x, 0.f);
+      const float2 z3n = make_float2(a3.x - r3, a3.y);  // a3 - r3
+      const float2 u3 = make_float2(r3 - z3n.x, -z3n.y);
+      const float2 x1 = a.x1[off];
+      float2 r0v;
+      r0v.x = x1.x + u3.x - 2.f * xh.x + v.x;
+      r0v.y = x1.y + u3.y - 2.f * xh.y + v.y;
+      a.z3[off] = z3n;
+      a.out[off] = r0v;
+      a.pdir[off] = r0v;
+      acc += (double)r0v.x * (double)r0v.x + (double)r0v.y * (double)r0v.y;
+    }
+  }
+  if (MODE == kRowOutCgQ) {
+    double tot;
+    if (reduce_last_block<1>(&acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], &tot)) {
+      sc->pqp = tot;
+      sc->alpha = (tot > 0.0) ? sc->rho / tot : 0.0;
+    }
+  } else if (MODE == kRowOutSdmm) {
+    double tot;
+    if (reduce_last_block<1>(&acc, partials + kCntRho0 * 2 * kMaxPartials, &sc->counter[kCntRho0], &tot)) {
+      sc->rho = tot;
+      sc->beta = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s) {
+  const FftShape rs = row_shape(c), cs = col_shape(c);
+  const size_t smr = (size_t)rs.nsig * c->L * sizeof(float2);
+  const size_t smc = (size_t)cs.nsig * c->L * sizeof(float2);
+  const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
+#define ROWF(E, MD)                                                                               \
+  k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan, c->n, \
+                                               rs.nsig, c->d_sc)
+  if (rs.ept == 8) {
+    if (mode == kRowInPlain) ROWF(8, kRowInPlain); else ROWF(8, kRowInCgDir);
+  } else {
+    if (mode == kRowInPlain) ROWF(12, kRowInPlain); else ROWF(12, kRowInCgDir);
+  }
+#undef ROWF
+  if (cs.ept == 8) {
+    allow_smem(k_col_fwd<8>, smc);
+    k_col_fwd<8><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig);
+  } else {
+    allow_smem(k_col_fwd<12>, smc);
+    k_col_fwd<12><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig);
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+template <int J>
+static void degrid_J(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
+  const int threads = 256;
+  int64_t blocks = (c->M + threads - 1) / threads;
+  if (blocks > kMaxPartials) blocks = kMaxPartials;
+#define DEG(MD)                                                                                  \
+  k_degrid<J, MD><<<(unsigned)blocks, threads, 0, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->kb, \
+                                                       c->ks, c->L, c->M, c->d_partials, c->d_sc)
+  if (mode == kDegridPerm) DEG(kDegridPerm);
+  else if (mode == kDegridSorted) DEG(kDegridSorted);
+  else DEG(kDegridSdmm);
+#undef DEG
+}
+
+int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
+  switch (c->J) {
+    case 2: degrid_J<2>(c, mode, a, s); break;
+    case 4: degrid_J<4>(c, mode, a, s); break;
+    case 6: degrid_J<6>(c, mode, a, s); break;
+    default: degrid_J<8>(c, mode, a, s); break;
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+template <int J>
+static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
+  const int threads = 256;
+  const size_t sm = 2 * (size_t)c->tileT * c->tileT * sizeof(float);
+  if (mode == kGridPerm)
+    k_grid<J, kGridPerm><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
+                                                         c->d_tile_list, c->d_tile_order, c->kb, c->ks, c->L,
+                                                         c->tileT, c->tiles_1d);
+  else
+    k_grid<J, kGridSorted><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
+                                                           c->d_tile_list, c->d_tile_order, c->kb, c->ks, c->L,
+                                                           c->tileT, c->tiles_1d);
+}
+
+int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
+  switch (c->J) {
+    case 2: grid_J<2>(c, mode, vis, s); break;
+    case 4: grid_J<4>(c, mode, vis, s); break;
+    case 6: grid_J<6>(c, mode, vis, s); break;
+    default: grid_J<8>(c, mode, vis, s); break;
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s) {
+  const FftShape rs = row_shape(c), cs = col_shape(c);
+  const size_t smr = (size_t)rs.nsig * c->L * sizeof(float2);
+  const size_t smc = (size_t)cs.nsig * c->L * sizeof(float2);
+  const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
+  if (cs.ept == 8) {
+    allow_smem(k_col_inv<8>, smc);
+    k_col_inv<8><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig);
+  } else {
+    allow_smem(k_col_inv<12>, smc);
+    k_col_inv<12><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig);
+  }
+#define ROWI(E, MD)                                                                                     \
+  k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan, c->n, rs.nsig, \
+                                               c->d_partials, c->d_sc)
+  if (rs.ept == 8) {
+    if (mode == kRowOutPlain) ROWI(8, kRowOutPlain);
+    else if (mode == kRowOutCgQ) ROWI(8, kRowOutCgQ);
+    else ROWI(8, kRowOutSdmm);
+  } else {
+    if (mode == kRowOutPlain) ROWI(12, kRowOutPlain);
+    else if (mode == kRowOutCgQ) ROWI(12, kRowOutCgQ);
+    else ROWI(12, kRowOutSdmm);
+  }
+#undef ROWI
+  return check_cuda(cudaGetLastError());
+}
+
+}  // namespace purify

@@ -1,0 +1,91 @@
+// Deterministic FP64 block reductions with a "last block finishes" epilogue.
+//
+// Every block writes its partial sums to a slot of a partial buffer, then
+// takes a ticket on a counter; the block that takes the last ticket sums the
+// partials in a fixed order and runs the finishing code.  The result does not
+// depend on block scheduling, and no extra kernel launch is needed.
+#pragma once
+
+#include "common.cuh"
+
+namespace purify {
+
+// Tree over the first `valid` lanes of a warp whose first `present` lanes
+// exist (any block size, including a partial last warp); every present lane
+// calls it, and the result is valid in lane 0.
+template <bool MAX>
+__device__ __forceinline__ double warp_tree(double v, int lane, int present, int valid) {
+  const unsigned mask = present >= 32 ? 0xffffffffu : ((1u << present) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(mask, v, o);
+    if (lane + o < valid) v = MAX ? fmax(v, t) : v + t;
+  }
+  return v;
+}
+
+// Sum (or max) of NV values over the block; the result is valid in thread 0.
+template <int NV, bool MAX = false>
+__device__ __forceinline__ void block_reduce(double* v) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  const int mylanes = min(32, (int)blockDim.x - wid * 32);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_tree<MAX>(v[k], lane, mylanes, mylanes);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double t = lane < nw ? sh[k][lane] : 0.0;
+      v[k] = warp_tree<MAX>(t, lane, mylanes, nw);
+    }
+  }
+}
+
+// Writes the block's NV partials, and in the last block to finish sums all
+// partials (fixed order) into total[0..NV).  Returns true in thread 0 of that
+// last block only.  partials holds NV x kMaxPartials doubles; the grid must
+// have at most kMaxPartials blocks.  The counter is reset for the next use.
+template <int NV, bool MAX = false>
+__device__ __forceinline__ bool reduce_last_block(double* v, double* partials, unsigned int* counter,
+                                                  double* total) {
+  __shared__ bool am_last;
+  const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_reduce<NV, MAX>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * kMaxPartials + bid] = v[k];
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    am_last = (ticket == nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (unsigned int i = threadIdx.x; i < nblk; i += blockDim.x) {
+      const double t = __ldcg(&partials[k * kMaxPartials + i]);
+      s = MAX ? fmax(s, t) : s + t;
+    }
+    acc[k] = s;
+  }
+  block_reduce<NV, MAX>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) total[k] = acc[k];
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+}  // namespace purify

@@ -1,0 +1,485 @@
+// SARA dictionary (§3.3): Psi = (1/sqrt q) [Dirac, db1, ..., db8], Psi^H its adjoint.
+//
+// Each Daubechies plane is a periodic, separable, orthonormal 2-D DWT in
+// Mallat layout.  One launch per level processes every wavelet basis at once
+// (grid.z = basis): a CTA loads the input region its coefficient tile needs
+// (with periodic wrap, also when the filter is longer than the signal),
+// filters rows then columns in shared memory, and writes the four sub-bands.
+// The synthesis runs the transpose level by level; its finest level sums all
+// bases and the Dirac plane in the same CTA, so x is written once.  In prox
+// mode the analysis epilogue applies the weighted soft threshold of §4.4
+// eq. prox1 and the dual update of Algorithm 1 steps 7-9 to each final
+// coefficient as it is produced, so alpha itself is never stored.
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace purify {
+
+constexpr int kTile = 16;     // coefficient tile (analysis) / half output tile (synthesis)
+constexpr int kMaxTaps = 16;  // db8
+
+struct LevelGeom {
+  int tile;     // coefficient tile side (analysis) / half output tile (synthesis); divides L/2
+  int n;        // image side (plane row stride)
+  int L;        // input side of this analysis level / output side of this synthesis level
+  int nb;       // wavelet planes in the launch
+  int plane0;   // index of the first wavelet plane in the coefficient array
+  int last;     // analysis: last level (LL goes to the plane); synthesis: finest level
+  float scale;  // 1 / sqrt(q)
+};
+
+struct BasisList {
+  int p[8];     // Daubechies order of wavelet plane k
+};
+
+__device__ __forceinline__ void load_filters(const WaveletFilters& wf, int p, float* h, float* g) {
+  const int len = 2 * p;
+  for (int m = threadIdx.x; m < len; m += blockDim.x) {
+    h[m] = wf.h[wf.off[p] + m];
+    const float hr = wf.h[wf.off[p] + len - 1 - m];
+    g[m] = (m & 1) ? -hr : hr;
+  }
+}
+
+// Soft threshold + dual update for one final coefficient alpha at index j.
+__device__ __forceinline__ double sara_prox(float2 al, size_t j, const SaraProxArgs& pa, float gamma) {
+  const float w = pa.w ? pa.w[j] : 1.0f;
+  const float2 z = pa.z1[j];
+  const float2 a = cadd(al, z);
+  const float mag = sqrtf(a.x * a.x + a.y * a.y);
+  const float shrink = fmaxf(mag - gamma * w, 0.0f);
+  const float s = mag > 0.0f ? shrink / mag : 0.0f;
+  const float2 r1 = cscale(a, s);
+  const float2 z1n = csub(a, r1);
+  pa.z1[j] = z1n;
+  pa.u1[j] = csub(r1, z1n);
+  return (double)w * sqrt((double)al.x * al.x + (double)al.y * al.y);
+}
+
+// ---------------------------------------------------------------------------
+// Dirac plane: alpha_0 = x / sqrt(q) (plain), or its prox update.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_dirac(const float2* __restrict__ x, float2* __restrict__ alpha, int64_t N, float scale,
+                        SaraProxArgs pa, double* partials, DevScalars* sc) {
+  double f1 = 0.0;
+  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const float2 al = cscale(x[j], scale);
+    if (MODE == kSaraPlain) alpha[j] = al;
+    else f1 += sara_prox(al, (size_t)j, pa, gamma);
+  }
+  if (MODE == kSaraProx) {
+    double tot;
+    if (reduce_last_block<1>(&f1, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot))
+      sc->f1 = tot;  // first contribution of this analysis
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One analysis level for every wavelet plane.
+//   input  : level 0: x (shared by all planes); else ll_in + k * (n/2)^2, L x L
+//   output : LH, HL, HH at their Mallat positions of plane k; LL to
+//            ll_out + k * (n/2)^2, or to the plane on the last level.
+// CTA: coefficient tile [I1, I1 + TI) x [I2, I2 + TI) of the L/2 x L/2 sub-bands.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in, int in_shared,
+                                                   float2* __restrict__ ll_out, float2* __restrict__ coef,
+                                                   LevelGeom G, BasisList bl, WaveletFilters wf,
+                                                   SaraProxArgs pa, double* partials, DevScalars* sc) {
+  __shared__ float h[kMaxTaps], g[kMaxTaps];
+  extern __shared__ float2 sm[];
+  const int k = blockIdx.z;
+  const int p = bl.p[k];
+  const int taps = 2 * p;
+  const int L = G.L, H = L / 2;
+  const int TI = G.tile;
+  const int I1 = blockIdx.y * TI, I2 = blockIdx.x * TI;
+  const int RH = 2 * TI + taps - 2;  // input rows/cols the tile needs
+  float2* inb = sm;                  // RH x RH
+  float2* rowp = sm + RH * RH;       // RH x 2TI  ([a | d] per input row)
+  load_filters(wf, p, h, g);
+  const float2* src = in_shared ? in : in + (size_t)k * (G.n / 2) * (G.n / 2);
+  for (int idx = threadIdx.x; idx < RH * RH; idx += blockDim.x) {
+    const int rr = idx / RH, cc = idx - rr * RH;
+    const int r = (2 * I1 + rr) % L, c = (2 * I2 + cc) % L;
+    inb[idx] = src[(size_t)r * L + c];
+  }
+  __syncthreads();
+  // rows: a[i2] = sum_m h[m] s[2 i2 + m], d[i2] = sum_m g[m] s[2 i2 + m]
+  for (int idx = threadIdx.x; idx < RH * TI; idx += blockDim.x) {
+    const int rr = idx / TI, i2 = idx - rr * TI;
+    const float2* s = inb + rr * RH + 2 * i2;
+    float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+    for (int m = 0; m < taps; ++m) {
+      const float2 v = s[m];
+      a.x = fmaf(h[m], v.x, a.x); a.y = fmaf(h[m], v.y, a.y);
+      d.x = fmaf(g[m], v.x, d.x); d.y = fmaf(g[m], v.y, d.y);
+    }
+    rowp[rr * (2 * TI) + i2] = a;
+    rowp[rr * (2 * TI) + TI + i2] = d;
+  }
+  __syncthreads();
+  // columns, and the write-out of the four sub-bands
+  float2* plane = coef + (size_t)(G.plane0 + k) * G.n * G.n;
+  float2* llk = ll_out + (size_t)k * (G.n / 2) * (G.n / 2);
+  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
+  double f1 = 0.0;
+  for (int idx = threadIdx.x; idx < TI * 2 * TI; idx += blockDim.x) {
+    const int i1 = idx / (2 * TI), kc = idx - i1 * (2 * TI);
+    float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
+    for (int m = 0; m < taps; ++m) {
+      const float2 v = rowp[(2 * i1 + m) * (2 * TI) + kc];
+      lo.x = fmaf(h[m], v.x, lo.x); lo.y = fmaf(h[m], v.y, lo.y);
+      hi.x = fmaf(g[m], v.x, hi.x); hi.y = fmaf(g[m], v.y, hi.y);
+    }
+    const int gi1 = I1 + i1;
+    const bool rowlow = kc < TI;
+    const int gi2 = I2 + (rowlow ? kc : kc - TI);
+    // lo: column-low; hi: column-high.  rowlow: the row-low half [a].
+    // LL = lo of a (top-left), LH = lo of d (top-right), HL = hi of a (bottom-left), HH = hi of d.
+    if (rowlow) {
+      if (G.last) {
+        const size_t j = (size_t)gi1 * G.n + gi2;
+        const float2 al = cscale(lo, G.scale);
+        if (MODE == kSaraPlain) plane[j] = al;
+        else f1 += sara_prox(al, (size_t)(G.plane0 + k) * G.n * G.n + j, pa, gamma);
+      } else {
+        llk[(size_t)gi1 * H + gi2] = lo;
+      }
+      const size_t j = (size_t)(H + gi1) * G.n + gi2;  // HL
+      const float2 al = cscale(hi, G.scale);
+      if (MODE == kSaraPlain) plane[j] = al;
+      else f1 += sara_prox(al, (size_t)(G.plane0 + k) * G.n * G.n + j, pa, gamma);
+    } else {
+      const size_t j1 = (size_t)gi1 * G.n + H + gi2;        // LH
+      const size_t j2 = (size_t)(H + gi1) * G.n + H + gi2;  // HH
+      const float2 a1 = cscale(lo, G.scale), a2 = cscale(hi, G.scale);
+      if (MODE == kSaraPlain) {
+        plane[j1] = a1;
+        plane[j2] = a2;
+      } else {
+        const size_t b = (size_t)(G.plane0 + k) * G.n * G.n;
+        f1 += sara_prox(a1, b + j1, pa, gamma);
+        f1 += sara_prox(a2, b + j2, pa, gamma);
+      }
+    }
+  }
+  if (MODE == kSaraProx) {
+    double tot;
+    if (reduce_last_block<1>(&f1, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot)) {
+      sc->f1 += tot;
+      if (G.last) {
+        // halting quantity zeta of §4.4 (after the last contribution)
+        const double prev = sc->f1_prev;
+        sc->zeta = (prev != 0.0) ? fabs(sc->f1 - prev) / fabs(prev) : INFINITY;
+        sc->f1_prev = sc->f1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One synthesis level for every wavelet plane (transpose of k_dwt_level):
+//   A  = colsyn(LL, HL), Dr = colsyn(LH, HH), s = rowsyn(A, Dr),
+//   s[k] = sum_{m = k mod 2} h[m] a[((k - m)/2) mod H] + g[m] d[((k - m)/2) mod H].
+// Output: L x L; to ll_out + k (n/2)^2, or, on the finest level, summed over
+// planes (plus the Dirac plane) into x, scaled by 1/sqrt(q).
+// CTA: output tile [K1, K1 + 2TO) x [K2, K2 + 2TO).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ ll_in, int ll_from_plane,
+                                                    float2* __restrict__ ll_out, const float2* __restrict__ coef,
+                                                    float2* __restrict__ x, int dirac_plane, LevelGeom G,
+                                                    BasisList bl, WaveletFilters wf) {
+  __shared__ float h[kMaxTaps], g[kMaxTaps];
+  extern __shared__ float2 sm[];
+  const int L = G.L, H = L / 2;
+  const int TO = G.tile;
+  const int K1 = blockIdx.y * 2 * TO, K2 = blockIdx.x * 2 * TO;
+  // the finest level loops over all planes in one CTA; otherwise one plane per z
+  const int kbeg = G.last ? 0 : blockIdx.z;
+  const int kend = G.last ? G.nb : blockIdx.z + 1;
+  float2 accum[16];  // up to (2TO)^2 / blockDim outputs per thread: 1024 / 256 = 4 (<= 16 for safety)
+  const int nout = (2 * TO) * (2 * TO);
+  for (int t = 0; t < 16; ++t) accum[t] = make_float2(0.f, 0.f);
+  for (int k = kbeg; k < kend; ++k) {
+    const int p = bl.p[k];
+    const int taps = 2 * p;
+    const int CW = TO + p - 1;                 // coefficient window per axis
+    float2* LLs = sm;                          // CW x CW each
+    float2* HLs = LLs + CW * CW;
+    float2* LHs = HLs + CW * CW;
+    float2* HHs = LHs + CW * CW;
+    float2* As = HHs + CW * CW;                // 2TO x CW
+    float2* Ds = As + 2 * TO * CW;             // 2TO x CW
+    __syncthreads();
+    load_filters(wf, p, h, g);
+    const float2* plane = coef + (size_t)(G.plane0 + k) * G.n * G.n;
+    const float2* llsrc = ll_from_plane ? plane : ll_in + (size_t)k * (G.n / 2) * (G.n / 2);
+    const int llstride = ll_from_plane ? G.n : H;
+    // window origin: coefficient K/2 - p + 1 (mod H)
+    const int o1 = K1 / 2 - p + 1, o2 = K2 / 2 - p + 1;
+    for (int idx = threadIdx.x; idx < CW * CW; idx += blockDim.x) {
+      const int t1 = idx / CW, t2 = idx - t1 * CW;
+      const int c1 = wrap(o1 + t1, H), c2 = wrap(o2 + t2, H);
+      LLs[idx] = llsrc[(size_t)c1 * llstride + c2];
+      HLs[idx] = plane[(size_t)(H + c1) * G.n + c2];
+      LHs[idx] = plane[(size_t)c1 * G.n + H + c2];
+      HHs[idx] = plane[(size_t)(H + c1) * G.n + H + c2];
+    }
+    __syncthreads();
+    // column synthesis: output row kappa1 in [0, 2TO), window column t2
+    for (int idx = threadIdx.x; idx < 2 * TO * CW; idx += blockDim.x) {
+      const int k1 = idx / CW, t2 = idx - k1 * CW;
+      float2 av = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
+      for (int m = (k1 & 1); m < taps; m += 2) {
+        const int t1 = (k1 - m) / 2 + p - 1;  // k1 - m even
+        const float2 ll = LLs[t1 * CW + t2], hl = HLs[t1 * CW + t2];
+        const float2 lh = LHs[t1 * CW + t2], hh = HHs[t1 * CW + t2];
+        av.x = fmaf(h[m], ll.x, fmaf(g[m], hl.x, av.x));
+        av.y = fmaf(h[m], ll.y, fmaf(g[m], hl.y, av.y));
+        dv.x = fmaf(h[m], lh.x, fmaf(g[m], hh.x, dv.x));
+        dv.y = fmaf(h[m], lh.y, fmaf(g[m], hh.y, dv.y));
+      }
+      As[idx] = av;
+      Ds[idx] = dv;
+    }
+    __syncthreads();
+    // row synthesis
+    int t = 0;
+    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
+      const int k1 = idx / (2 * TO), k2 = idx - k1 * (2 * TO);
+      float2 s = make_float2(0.f, 0.f);
+      for (int m = (k2 & 1); m < taps; m += 2) {
+        const int t2 = (k2 - m) / 2 + p - 1;
+        const float2 av = As[k1 * CW + t2], dv = Ds[k1 * CW + t2];
+        s.x = fmaf(h[m], av.x, fmaf(g[m], dv.x, s.x));
+        s.y = fmaf(h[m], av.y, fmaf(g[m], dv.y, s.y));
+      }
+      if (G.last) {
+        accum[t] = cadd(accum[t], s);
+      } else {
+        const int gk1 = K1 + k1, gk2 = K2 + k2;
+        if (gk1 < L && gk2 < L) ll_out[(size_t)k * (G.n / 2) * (G.n / 2) + (size_t)gk1 * L + gk2] = s;
+      }
+    }
+  }
+  if (G.last) {
+    int t = 0;
+    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
+      const int k1 = idx / (2 * TO), k2 = idx - k1 * (2 * TO);
+      const int gk1 = K1 + k1, gk2 = K2 + k2;
+      if (gk1 < L && gk2 < L) {
+        float2 s = accum[t];
+        const size_t j = (size_t)gk1 * G.n + gk2;
+        if (dirac_plane >= 0) s = cadd(s, coef[(size_t)dirac_plane * G.n * G.n + j]);
+        x[j] = cscale(s, G.scale);
+      }
+    }
+  }
+}
+
+// Dirac-only synthesis: x = alpha_0 / sqrt(q).
+__global__ void k_dirac_syn(const float2* __restrict__ a, float2* __restrict__ x, int64_t N, float scale) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+    x[j] = cscale(a[j], scale);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static void basis_layout(const purify_ctx* c, int& dirac_plane, int& plane0, BasisList& bl, int& nb) {
+  dirac_plane = -1;
+  nb = 0;
+  plane0 = 0;
+  for (int k = 0; k < c->q; ++k) {
+    if (c->bases[k] == 0) dirac_plane = k;
+    else {
+      if (nb == 0) plane0 = k;
+      bl.p[nb++] = c->bases[k];
+    }
+  }
+}
+
+// Largest divisor of H that is at most kTile.
+static int tile_for(int H) {
+  for (int t = std::min(kTile, H); t > 1; --t)
+    if (H % t == 0) return t;
+  return 1;
+}
+
+// Finish zeta when the dictionary has no wavelet plane (Dirac only).
+__global__ void k_finish_zeta(DevScalars* sc) {
+  const double prev = sc->f1_prev;
+  sc->zeta = (prev != 0.0) ? fabs(sc->f1 - prev) / fabs(prev) : INFINITY;
+  sc->f1_prev = sc->f1;
+}
+
+static size_t dwt_smem(int TI, int taps) {
+  const int RH = 2 * TI + taps - 2;
+  return (size_t)(RH * RH + RH * 2 * TI) * sizeof(float2);
+}
+
+static size_t idwt_smem(int TO, int p) {
+  const int CW = TO + p - 1;
+  return (size_t)(4 * CW * CW + 2 * 2 * TO * CW) * sizeof(float2);
+}
+
+int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, const SaraProxArgs& pa,
+                  cudaStream_t s) {
+  int dirac_plane, plane0, nb;
+  BasisList bl{};
+  basis_layout(c, dirac_plane, plane0, bl, nb);
+  const int64_t N = (int64_t)c->n * c->n;
+  const float scale = 1.0f / sqrtf((float)c->q);
+  if (dirac_plane >= 0) {
+    int blocks = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    if (mode == kSaraPlain)
+      k_dirac<kSaraPlain><<<blocks, 256, 0, s>>>(x, alpha + (size_t)dirac_plane * N, N, scale, pa,
+                                                 c->d_partials, c->d_sc);
+    else {
+      SaraProxArgs pd = pa;  // prox arrays are indexed over the whole coefficient vector
+      k_dirac<kSaraProx><<<blocks, 256, 0, s>>>(x, nullptr, N, scale, pd, c->d_partials, c->d_sc);
+    }
+  } else if (mode == kSaraProx) {
+    cudaMemsetAsync(&c->d_sc->f1, 0, sizeof(double), s);
+  }
+  if (nb == 0) {
+    if (mode == kSaraProx) k_finish_zeta<<<1, 1, 0, s>>>(c->d_sc);
+    return check_cuda(cudaGetLastError());
+  }
+  int maxp = 1;
+  for (int k = 0; k < nb; ++k) maxp = std::max(maxp, bl.p[k]);
+  for (int lev = 0; lev < c->levels; ++lev) {
+    const int L = c->n >> lev;
+    const int H = L / 2;
+    const int TI = tile_for(H);
+    LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale};
+    const float2* in = (lev == 0) ? x : c->d_ll[(lev - 1) & 1];
+    float2* llo = c->d_ll[lev & 1];
+    dim3 grid(H / TI, H / TI, nb);
+    const size_t sm = dwt_smem(TI, 2 * maxp);
+    if (mode == kSaraPlain)
+      k_dwt_level<kSaraPlain><<<grid, 256, sm, s>>>(in, lev == 0, llo, alpha, G, bl, c->wf, pa, c->d_partials,
+                                                     c->d_sc);
+    else
+      k_dwt_level<kSaraProx><<<grid, 256, sm, s>>>(in, lev == 0, llo, pa.z1, G, bl, c->wf, pa, c->d_partials,
+                                                    c->d_sc);
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s) {
+  int dirac_plane, plane0, nb;
+  BasisList bl{};
+  basis_layout(c, dirac_plane, plane0, bl, nb);
+  const int64_t N = (int64_t)c->n * c->n;
+  const float scale = 1.0f / sqrtf((float)c->q);
+  if (nb == 0) {
+    int blocks = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    k_dirac_syn<<<blocks, 256, 0, s>>>(alpha + (size_t)dirac_plane * N, x, N, scale);
+    return check_cuda(cudaGetLastError());
+  }
+  int maxp = 1;
+  for (int k = 0; k < nb; ++k) maxp = std::max(maxp, bl.p[k]);
+  for (int lev = c->levels - 1; lev >= 0; --lev) {
+    const int L = c->n >> lev;  // output side
+    const int H = L / 2;
+    const int TO = tile_for(H);
+    LevelGeom G{TO, c->n, L, nb, plane0, lev == 0, scale};
+    const bool from_plane = (lev == c->levels - 1);
+    const float2* llin = from_plane ? nullptr : c->d_ll[(lev + 1) & 1];
+    float2* llo = c->d_ll[lev & 1];
+    dim3 grid(L / (2 * TO), L / (2 * TO), lev == 0 ? 1 : nb);
+    const size_t sm = idwt_smem(TO, maxp);
+    k_idwt_level<<<grid, 256, sm, s>>>(llin, from_plane, llo, alpha, x, dirac_plane, G, bl, c->wf);
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Daubechies filters by spectral factorisation (Daubechies 1988): the roots y_k
+// of P(y) = sum_{k<p} C(p-1+k, k) y^k (Durand-Kerner iteration), each mapped to
+// the zero inside the unit circle of z^2 - (2 - 4y) z + 1; h is the coefficient
+// list of (z + 1)^p prod (z - z_k) in descending powers, scaled to sum sqrt(2).
+// ---------------------------------------------------------------------------
+static std::vector<double> daubechies(int p) {
+  using cd = std::complex<double>;
+  const int d = p - 1;
+  std::vector<double> P(p);
+  double binom = 1.0;  // C(p-1+k, k)
+  for (int k = 0; k < p; ++k) {
+    if (k > 0) binom = binom * (double)(p - 1 + k) / (double)k;
+    P[k] = binom;
+  }
+  std::vector<cd> roots(d);
+  if (d > 0) {
+    // monic in y: divide by the leading coefficient P[d]
+    std::vector<cd> r(d);
+    const cd seed(0.4, 0.9);
+    cd pw(1.0, 0.0);
+    for (int k = 0; k < d; ++k) { r[k] = pw; pw *= seed; }
+    auto evalP = [&](cd y) {
+      cd acc = P[d];
+      for (int k = d - 1; k >= 0; --k) acc = acc * y + P[k];
+      return acc / P[d];
+    };
+    for (int it = 0; it < 2000; ++it) {
+      double delta = 0.0;
+      for (int k = 0; k < d; ++k) {
+        cd den(1.0, 0.0);
+        for (int j = 0; j < d; ++j)
+          if (j != k) den *= (r[k] - r[j]);
+        const cd step = evalP(r[k]) / den;
+        r[k] -= step;
+        delta = std::max(delta, std::abs(step));
+      }
+      if (delta < 1e-17) break;
+    }
+    roots = r;
+  }
+  // polynomial coefficients in ascending powers of z
+  std::vector<cd> poly(1, cd(1.0, 0.0));
+  auto mul_root = [&](cd z0) {  // poly *= (z - z0)
+    std::vector<cd> out(poly.size() + 1, cd(0.0, 0.0));
+    for (size_t i = 0; i < poly.size(); ++i) {
+      out[i + 1] += poly[i];
+      out[i] -= z0 * poly[i];
+    }
+    poly.swap(out);
+  };
+  for (int k = 0; k < p; ++k) mul_root(cd(-1.0, 0.0));
+  for (int k = 0; k < d; ++k) {
+    const cd c = 2.0 - 4.0 * roots[k];
+    const cd disc = std::sqrt(c * c - 4.0);
+    cd z1 = (c + disc) / 2.0, z2 = (c - disc) / 2.0;
+    mul_root(std::abs(z1) < 1.0 ? z1 : z2);
+  }
+  // descending powers: h[m] = coefficient of z^(2p-1-m)
+  std::vector<double> h(2 * p);
+  double sum = 0.0;
+  for (int m = 0; m < 2 * p; ++m) {
+    h[m] = poly[2 * p - 1 - m].real();
+    sum += h[m];
+  }
+  for (auto& v : h) v *= std::sqrt(2.0) / sum;
+  return h;
+}
+
+void make_daubechies(WaveletFilters& wf) {
+  int off = 0;
+  wf.off[0] = 0;
+  for (int p = 1; p <= 8; ++p) {
+    wf.off[p] = off;
+    std::vector<double> h = daubechies(p);
+    for (int m = 0; m < 2 * p; ++m) wf.h[off + m] = (float)h[m];
+    off += 2 * p;
+  }
+}
+
+}  // namespace purify

@@ -1,0 +1,260 @@
+// Entrywise proximity operators, projections, CG vector updates and reductions.
+//
+// §4.5 notes that the proximity operators are entrywise and parallel; each
+// kernel here is one pass over its vectors with the FP64 reduction it needs
+// finished by the last block (reduce.cuh), so a scalar such as a CG step size
+// is ready on the device for the next kernel without a host round trip.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace purify {
+
+static unsigned blocks_for(int64_t n, int threads = 256, int cap = 2048) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// §4.4 eq. prox1: a/|a| (|a| - gamma w)^+, with gamma from the host or the device.
+__global__ void k_soft(int64_t n, const float2* __restrict__ in, const float* __restrict__ w,
+                       const double* gamma_dev, float gamma, float2* __restrict__ out) {
+  const float gm = gamma_dev ? (float)*gamma_dev : gamma;
+  GRID_STRIDE(j, n) {
+    const float2 a = in[j];
+    const float lam = gm * (w ? w[j] : 1.0f);
+    const float mag = sqrtf(a.x * a.x + a.y * a.y);
+    const float s = mag > 0.0f ? fmaxf(mag - lam, 0.0f) / mag : 0.0f;
+    out[j] = cscale(a, s);
+  }
+}
+
+// ||a - b||^2 in FP64 -> sc->norm2
+__global__ void k_norm_diff(int64_t n, const float2* __restrict__ a, const float2* __restrict__ b,
+                            double* partials, DevScalars* sc) {
+  double acc = 0.0;
+  GRID_STRIDE(j, n) {
+    const double dx = (double)a[j].x - (double)b[j].x, dy = (double)a[j].y - (double)b[j].y;
+    acc += dx * dx + dy * dy;
+  }
+  double tot;
+  if (reduce_last_block<1>(&acc, partials + kCntNorm * 2 * kMaxPartials, &sc->counter[kCntNorm], &tot))
+    sc->norm2 = tot;
+}
+
+// Projection onto {r : ||r - y|| <= eps} given ||in - y||^2 on the device.
+__global__ void k_l2_project(int64_t n, const float2* __restrict__ in, const float2* __restrict__ y, double eps,
+                             const double* norm2, float2* __restrict__ out) {
+  const double nd = sqrt(*norm2);
+  const float scale = (nd > eps) ? (float)(eps / nd) : 1.0f;
+  GRID_STRIDE(j, n) {
+    const float2 yy = y[j], r = in[j];
+    out[j] = make_float2(fmaf(scale, r.x - yy.x, yy.x), fmaf(scale, r.y - yy.y, yy.y));
+  }
+}
+
+// §4.4 eq. prox3 with complex entries as real pairs: max(Re a, 0).
+__global__ void k_positive(int64_t n, const float2* __restrict__ in, float2* __restrict__ out) {
+  GRID_STRIDE(j, n) out[j] = make_float2(fmaxf(in[j].x, 0.f), 0.f);
+}
+
+// CG: x += alpha p; r -= alpha Qp; rho' = ||r||^2; beta = rho'/rho.
+__global__ void k_cg_update(int64_t n, float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
+                            const float2* __restrict__ qp, double* partials, DevScalars* sc) {
+  const float al = (float)sc->alpha;
+  double acc = 0.0;
+  GRID_STRIDE(j, n) {
+    const float2 pj = p[j], qj = qp[j];
+    float2 xj = x[j], rj = r[j];
+    xj.x = fmaf(al, pj.x, xj.x);
+    xj.y = fmaf(al, pj.y, xj.y);
+    rj.x = fmaf(-al, qj.x, rj.x);
+    rj.y = fmaf(-al, qj.y, rj.y);
+    x[j] = xj;
+    r[j] = rj;
+    acc += (double)rj.x * rj.x + (double)rj.y * rj.y;
+  }
+  double tot;
+  if (reduce_last_block<1>(&acc, partials + kCntRho * 2 * kMaxPartials, &sc->counter[kCntRho], &tot)) {
+    sc->beta = (sc->rho > 0.0) ? tot / sc->rho : 0.0;
+    sc->rho = tot;
+    sc->cg_res = sqrt(tot);
+  }
+}
+
+// r = b - Qx; p = r; rho = ||r||^2 (the start of purify_cg_solve).
+__global__ void k_cg_residual_init(int64_t n, const float2* __restrict__ b, const float2* __restrict__ qx,
+                                   float2* __restrict__ r, float2* __restrict__ p, double* partials,
+                                   DevScalars* sc) {
+  double acc = 0.0;
+  GRID_STRIDE(j, n) {
+    const float2 v = csub(b[j], qx[j]);
+    r[j] = v;
+    p[j] = v;
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  double tot;
+  if (reduce_last_block<1>(&acc, partials + kCntRho0 * 2 * kMaxPartials, &sc->counter[kCntRho0], &tot)) {
+    sc->rho = tot;
+    sc->beta = 0.0;
+    sc->cg_res = sqrt(tot);
+  }
+}
+
+// max |a_j| -> sc->amax
+__global__ void k_max_abs(int64_t n, const float2* __restrict__ a, double* partials, DevScalars* sc) {
+  double m = 0.0;
+  GRID_STRIDE(j, n) m = fmax(m, sqrt((double)a[j].x * a[j].x + (double)a[j].y * a[j].y));
+  double tot;
+  if (reduce_last_block<1, true>(&m, partials + kCntMax * 2 * kMaxPartials, &sc->counter[kCntMax], &tot))
+    sc->amax = tot;
+}
+
+// SDMM l2 branch (Algorithm 1 steps 7-9, i = 2) after the degridding kernel
+// left s2 = Phi x_hat and ||s2 + z2 - y||^2 on the device:
+//   a = s2 + z2; r2 = y + min(1, eps/||a - y||)(a - y); z2 <- a - r2;
+//   u2 = r2 - z2; v = u2 - s2 (gridded next: Phi^H v = x2 - Phi^H Phi x_hat).
+__global__ void k_sdmm_l2(int64_t M, const float2* __restrict__ s2, float2* __restrict__ z2,
+                          const float2* __restrict__ y, const uint16_t* __restrict__ yb,
+                          const float* __restrict__ yscale, float2* __restrict__ v, const DevScalars* sc) {
+  const double nd = sqrt(sc->l2_dn2);
+  const float scale = (nd > sc->eps) ? (float)(sc->eps / nd) : 1.0f;
+  GRID_STRIDE(i, M) {
+    float2 yy;
+    if (y) {
+      yy = y[i];
+    } else {
+      const float s4 = yscale[i >> 12];
+      const uint32_t bits = reinterpret_cast<const uint32_t*>(yb)[i];
+      yy = make_float2(__uint_as_float(bits << 16) * s4, __uint_as_float(bits & 0xffff0000u) * s4);
+    }
+    const float2 s = s2[i];
+    const float2 a = cadd(s, z2[i]);
+    const float2 r2 = make_float2(fmaf(scale, a.x - yy.x, yy.x), fmaf(scale, a.y - yy.y, yy.y));
+    const float2 zn = csub(a, r2);
+    z2[i] = zn;
+    v[i] = csub(csub(r2, zn), s);
+  }
+}
+
+// Reweighting (§3.3): w = delta / (delta + |alpha|).
+__global__ void k_reweight(int64_t n, const float2* __restrict__ alpha, float* __restrict__ w, int round,
+                           const DevScalars* sc) {
+  const double amax = sc->amax;
+  const double delta = fmax(pow(10.0, -(double)round) * amax, 1e-6 * amax);
+  GRID_STRIDE(j, n) {
+    if (delta == 0.0) {
+      w[j] = 1.0f;
+    } else {
+      const double a = sqrt((double)alpha[j].x * alpha[j].x + (double)alpha[j].y * alpha[j].y);
+      w[j] = (float)(delta / (delta + a));
+    }
+  }
+}
+
+__global__ void k_gather(int64_t n, const float2* __restrict__ src, const int* __restrict__ perm,
+                         float2* __restrict__ dst) {
+  GRID_STRIDE(i, n) dst[i] = src[perm[i]];
+}
+
+// bf16 storage of y: one CTA per block of 4096 visibilities, scale = max |component|.
+__global__ void __launch_bounds__(256) k_quantize_bf16(int64_t M, const float2* __restrict__ y,
+                                                       uint32_t* __restrict__ yb, float* __restrict__ yscale) {
+  __shared__ float wmax[8];
+  const int64_t b0 = (int64_t)blockIdx.x * 4096;
+  const int64_t b1 = min(b0 + 4096, M);
+  float m = 0.f;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) m = fmaxf(m, fmaxf(fabsf(y[i].x), fabsf(y[i].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, wmax[k]);
+  const float sc = m > 0.f ? m : 1.f;
+  if (threadIdx.x == 0) yscale[blockIdx.x] = sc;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const __nv_bfloat16 re = __float2bfloat16_rn(y[i].x / sc);
+    const __nv_bfloat16 im = __float2bfloat16_rn(y[i].y / sc);
+    yb[i] = (uint32_t)__bfloat16_as_ushort(re) | ((uint32_t)__bfloat16_as_ushort(im) << 16);
+  }
+}
+
+__global__ void k_set_gamma(DevScalars* sc, double beta) { sc->gamma = beta * sc->amax; }
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_soft_threshold(int64_t count, const float2* in, const float* w, const double* gamma_dev, float gamma,
+                          float2* out, cudaStream_t s) {
+  k_soft<<<blocks_for(count), 256, 0, s>>>(count, in, w, gamma_dev, gamma, out);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_l2_norm_diff(purify_ctx* c, int64_t count, const float2* a, const float2* b, cudaStream_t s) {
+  k_norm_diff<<<blocks_for(count), 256, 0, s>>>(count, a, b, c->d_partials, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_l2_project(int64_t count, const float2* in, const float2* y, double eps, const double* norm2_dev,
+                      float2* out, cudaStream_t s) {
+  k_l2_project<<<blocks_for(count), 256, 0, s>>>(count, in, y, eps, norm2_dev, out);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s) {
+  k_positive<<<blocks_for(count), 256, 0, s>>>(count, in, out);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_cg_update(purify_ctx* c, float2* x, float2* r, const float2* p, const float2* qp, cudaStream_t s) {
+  const int64_t N = (int64_t)c->n * c->n;
+  k_cg_update<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, qp, c->d_partials, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, float2* p,
+                            cudaStream_t s) {
+  const int64_t N = (int64_t)c->n * c->n;
+  k_cg_residual_init<<<blocks_for(N), 256, 0, s>>>(N, b, qx, r, p, c->d_partials, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s) {
+  k_max_abs<<<blocks_for(count), 256, 0, s>>>(count, a, c->d_partials, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s) {
+  purify_ctx* c = st->ctx;
+  k_sdmm_l2<<<blocks_for(c->M), 256, 0, s>>>(c->M, st->s2, st->z2, st->y_bf16 ? nullptr : st->y, st->yb,
+                                             st->yscale, st->v, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round, cudaStream_t s) {
+  k_reweight<<<blocks_for(count), 256, 0, s>>>(count, alpha, w, round, c->d_sc);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_gather_perm(int64_t M, const float2* src, const int* perm, float2* dst, cudaStream_t s) {
+  k_gather<<<blocks_for(M), 256, 0, s>>>(M, src, perm, dst);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_quantize_bf16(int64_t M, const float2* y, uint16_t* yb, float* yscale, cudaStream_t s) {
+  const int64_t blocks = (M + 4095) / 4096;
+  k_quantize_bf16<<<(unsigned)blocks, 256, 0, s>>>(M, y, reinterpret_cast<uint32_t*>(yb), yscale);
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_set_gamma(purify_ctx* c, double beta, cudaStream_t s) {
+  k_set_gamma<<<1, 1, 0, s>>>(c->d_sc, beta);
+  return check_cuda(cudaGetLastError());
+}
+
+}  // namespace purify

@@ -1,0 +1,141 @@
+"""GPU parity of the operators against the FP64 oracle (needs a GB300).
+
+Phi, Phi^H (§5 eq. opmodel), Psi, Psi^H (§3.3) and the proximity operators
+(§4.4) of the CUDA library, called through the C ABI, against the oracle on
+the same seeded complex64 / float32 inputs.  Bound: relative l2 error <= 1e-5
+for the FP32 operators; the prox outputs to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import measurement as me, prox as oprox, sara as osara, cg as ocg
+from paper_1307_4370_gb300 import inputs
+
+from gpu_util import dev, host, rel_err, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+# (n, M, J, coverage): several FFT tiles, radix-3 grids (2n = 192, 384), ragged M,
+# the 64 x 64 and 256 x 256 workloads at full size.
+PHI_CASES = [
+    (8, 37, 2, "uniform"),
+    (16, 500, 6, "uniform"),
+    (32, 1000, 8, "uniform"),
+    (64, 2048, 4, "sdmm64"),
+    (96, 3001, 6, "gauss"),
+    (192, 20000, 4, "gauss"),
+    (256, 65536, 6, "sdmm256"),
+]
+
+
+def coverage(kind, n, M, rng):
+    if kind == "uniform":
+        return inputs.uniform_uv(M, rng)
+    if kind == "gauss":
+        return inputs.uv_variable_density(M, n, rng).astype(np.float32).astype(np.float64)
+    return inputs.make_problem(kind).uv
+
+
+@pytest.mark.parametrize("n,M,J,kind", PHI_CASES)
+def test_phi_and_adjoint(n, M, J, kind):
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(n + M)
+    uv = coverage(kind, n, M, rng)
+    x = inputs.random_image(n, rng)
+    v = inputs.random_vis(M, rng)
+    ctx = binding.Context(n, uv.astype(np.float32), J=J, levels=min(4, int(np.log2(n)) - 1))
+    y = host(ctx.phi(dev(x, torch)))
+    xa = host(ctx.phi_adj(dev(v, torch)))
+    assert rel_err(y, me.phi(x, uv, J)) <= TOL
+    assert rel_err(xa, me.phi_adj(v, uv, n, J)) <= TOL
+    # repeated calls give the same result (the scratch grid is fully rewritten)
+    y2 = host(ctx.phi(dev(x, torch)))
+    assert rel_err(y2, y) <= 1e-6
+
+
+def test_phi_large_sampled():
+    """1024 x 1024, M = 2^21 (the mixed-precision workload's sizes), all outputs."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p = inputs.make_problem("sdmm1024")
+    w = p.workload
+    rng = np.random.default_rng(3)
+    x = inputs.random_image(w.n, rng)
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    y = host(ctx.phi(dev(x, torch)))
+    idx = rng.choice(w.M, 20000, replace=False)
+    want = me.phi(x, p.uv, w.J)
+    assert rel_err(y, want) <= TOL
+    assert rel_err(y[idx], want[idx]) <= TOL
+    v = inputs.random_vis(w.M, rng)
+    xa = host(ctx.phi_adj(dev(v, torch)))
+    assert rel_err(xa, me.phi_adj(v, p.uv, w.n, w.J)) <= TOL
+
+
+@pytest.mark.parametrize("n,levels,mask", [(16, 4, 0x1FF), (64, 4, 0x1FF), (96, 4, 0x1FF), (192, 4, 0x1FF),
+                                           (256, 4, 0x1FF), (64, 3, 0x100), (32, 2, 0x001), (64, 4, 0x0F5),
+                                           (8, 3, 0x1FF)])
+def test_sara(n, levels, mask):
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(n * 7 + levels)
+    bases = tuple(b for b in range(9) if mask >> b & 1)
+    uv = inputs.uniform_uv(16, rng)
+    ctx = binding.Context(n, uv.astype(np.float32), J=4, levels=levels, bases_mask=mask)
+    x = inputs.random_image(n, rng)
+    al = host(ctx.sara_analysis(dev(x, torch)))
+    assert al.shape == (len(bases), n, n)
+    assert rel_err(al, osara.sara_analysis(x, levels, bases)) <= TOL
+    b = rng.standard_normal((len(bases), n, n)) + 1j * rng.standard_normal((len(bases), n, n))
+    b = b.astype(np.complex64).astype(np.complex128)
+    xs = host(ctx.sara_synthesis(dev(b, torch)))
+    assert rel_err(xs, osara.sara_synthesis(b, levels, bases)) <= TOL
+
+
+def test_prox_operators():
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(9)
+    ctx = binding.Context(16, inputs.uniform_uv(8, rng).astype(np.float32), J=4)
+    for count in (0, 1, 1000, 300001):
+        a = inputs.random_vis(count, rng)
+        w = rng.uniform(0, 2, count).astype(np.float32).astype(np.float64)
+        gamma = 0.7
+        if count == 0:
+            continue
+        got = host(ctx.prox_l1_reweighted(dev(a, torch), dev(w, torch), gamma))
+        want = oprox.soft_threshold(a, np.float32(gamma) * w)
+        assert np.max(np.abs(got - want)) <= 1e-6 * max(1.0, np.abs(a).max())
+        got1 = host(ctx.prox_l1_reweighted(dev(a, torch), None, gamma))
+        assert np.max(np.abs(got1 - oprox.soft_threshold(a, gamma))) <= 1e-6 * max(1.0, np.abs(a).max())
+        y = inputs.random_vis(count, rng)
+        for eps in (0.5 * np.sqrt(count), 10.0 * np.sqrt(count)):  # outside / inside the ball
+            nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+            got = host(ctx.proj_l2ball(dev(a, torch), dev(y, torch), eps, norm_out=nrm))
+            assert rel_err(got, oprox.project_l2_ball(a, y, eps)) <= 1e-6
+            assert float(nrm.item()) == pytest.approx(np.linalg.norm(a - y), rel=1e-9)
+        got = host(ctx.proj_positive(dev(a, torch)))
+        assert np.array_equal(got, oprox.project_positive(a))
+
+
+@pytest.mark.parametrize("n,M,J,iters", [(16, 300, 4, 40), (64, 2048, 4, 10), (256, 65536, 6, 10)])
+def test_cg_solve(n, M, J, iters):
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(n + iters)
+    uv = inputs.uniform_uv(M, rng)
+    ctx = binding.Context(n, uv.astype(np.float32), J=J)
+    b = inputs.random_image(n, rng)
+    x0 = inputs.random_image(n, rng)
+    x, res = ctx.cg_solve(dev(b, torch), dev(x0, torch), iters)
+    want, want_res = ocg.cg(lambda v: me.phi_adj(me.phi(v, uv, J), uv, n, J) + 2.0 * v, b, x0, iters)
+    assert rel_err(host(x).reshape(n, n), want) <= 1e-5
+    assert float(res.item()) == pytest.approx(want_res, rel=1e-3, abs=1e-6 * np.linalg.norm(b))
