@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the SDMM-SARA hot path on GB300.
+
+Workload (default ``sdmm256``): 256 x 256 image of 200 Gaussian sources plus a
+k^-2 diffuse field, M = 65536 variable-density visibilities, Kaiser-Bessel
+6 x 6, 512 x 512 grid, FP32 with FP64 reductions, SARA (Dirac + db1..db8,
+4 levels), 10 CG steps per x-update, reweighting every 60 iterations (five
+rounds in 300 iterations).  One step = one SDMM iteration (Algorithm 1
+steps 5-9).  Inputs are seeded and synthetic.
+
+Printed: one JSON line with SDMM iterations/s (device-timed, inputs resident,
+L2 flushed between steps), the Phi + Phi^H visibility rate, the end-to-end
+rate through the C ABI with host buffers, the roofline of the dominant kernel,
+the FP64 CPU oracle as a reported baseline, SM clocks and kernel launches.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on the same
+workload and metric.  Under torchrun each rank solves its own independent
+problem (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1307_4370_gb300 import inputs  # noqa: E402
+
+REWEIGHT_EVERY = 60
+ROUNDS = 5
+L2_FLUSH_BYTES = 512 << 20
+METRIC = "SDMM-SARA iterations/sec"
+UNIT = "iterations/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sdmm256", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+def workload_config(w: inputs.Workload) -> dict:
+    return {"workload": f"{w.name}: {w.n}x{w.n} image, M={w.M} visibilities, KB {w.J}x{w.J}, "
+                        f"{2 * w.n}x{2 * w.n} grid, SARA 9 bases x 4 levels, CG {w.cg_iters} steps",
+            "n": w.n, "M": w.M, "J": w.J, "cg_iters": w.cg_iters,
+            "reweight_every": REWEIGHT_EVERY, "rounds": ROUNDS}
+
+
+# ---------------------------------------------------------------------------
+# FP64 CPU oracle: the reported baseline (and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None):
+    """SDMM iterations/s of the FP64 oracle on a bounded sample of the workload."""
+    from oracle import sdmm as osdmm, simulate
+
+    p = inputs.make_problem(w)
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db)
+    ops = simulate.operators(p.uv, w.n, w.J)
+    st = osdmm.init_state(ops, y, (w.n, w.n))
+    wts = np.ones((9, w.n, w.n))
+    osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)  # the first iteration is trivial (x_hat = 0)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_iters is not None and done >= max_iters):
+            break
+    return done / el, done, el
+
+
+def cpu_baseline_entry(w, budget_s, max_iters=None) -> dict:
+    rate, done, el = oracle_rate(w, budget_s, max_iters)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} SDMM iterations (after one untimed) of the {w.name} workload, FP64 numpy "
+                      f"oracle, single thread, {el:.1f} s; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # bounded: about a minute of oracle work whatever --steps is
+    budget = min(60.0, max(10.0, 0.2 * (args.steps + args.warmup)))
+    entry = cpu_baseline_entry(w, budget)
+    out = {"impl": "reference", "metric": METRIC, "value": entry["value"], "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / entry["value"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(w),
+           "cpu_baseline": entry,
+           "e2e": {"value": entry["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
+    """Unique bytes each kernel family must move per launch (averaged over the
+    launches of one SDMM step); complex64 = 8 B, uv = 8 B per visibility."""
+    N, M, k = w.n * w.n, w.M, w.cg_iters
+    c = 8
+    D = q * N
+    return {
+        # read x (or r, p; write p in CG steps), write n x 2n rows
+        "row_fwd": (k * (5 * N * c) + 3 * N * c) / (k + 1),
+        "col_fwd": 6 * N * c,                          # read n x 2n, write 2n x 2n
+        "degrid": (k * (4 * N * c + 2 * M * c) + (4 * N * c + 4 * M * c)) / (k + 1),
+        "grid": 4 * N * c + 2 * M * c,                 # read uv + vis, write the grid
+        "col_inv": 6 * N * c,
+        "row_inv": (k * (5 * N * c) + 9 * N * c) / (k + 1),
+        "cg_update": 6 * N * c,
+        "sdmm_l2": 5 * M * c,                          # s2, z2, y in; z2, v out
+        # all levels of all planes: x in, z1 / w in, z1 / u1 out (w float32)
+        "dwt_level": (N * c + D * (c + 4 + 2 * c)) / 4,
+        "idwt_level": (D * c + N * c) / 4,
+        "dirac": 4 * N * c,
+    }
+
+
+def peaks() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1307_4370_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cpu_entry = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds)
+
+    # each rank: its own independent problem of the same shape
+    wr = inputs.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})
+    p = inputs.make_problem(wr)
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    x_true = torch.tensor(p.x_true.astype(np.complex64), device=dev)
+    y0 = ctx.phi(x_true)
+    sig = float(torch.linalg.vector_norm(y0).item()) / math.sqrt(w.M) * 10 ** (-w.isnr_db / 20)
+    noise = torch.tensor(p.noise_unit.astype(np.complex64), device=dev)
+    y = y0 + sig * noise
+    eps = binding.l2_bound(w.M, sig)
+    st = ctx.sdmm_state()
+    st.init(y, eps, cg_iters=w.cg_iters)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    state = {"iters": 0, "round": 0}
+
+    def one_step():
+        if state["iters"] > 0 and state["iters"] % REWEIGHT_EVERY == 0 and state["round"] < ROUNDS - 1:
+            state["round"] += 1
+            st.reweight(state["round"])
+        st.step()
+        state["iters"] += 1
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-timed steps (value) -------------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = binding.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))                # evict L2 between steps (not timed)
+        evs[k][0].record(stream)
+        one_step()
+        evs[k][1].record(stream)
+    barrier()
+    gpu_launches = binding.launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # --- Phi + Phi^H visibility rate (public calls, L2 flushed) ----------
+    xr = torch.randn(w.n, w.n, dtype=torch.complex64, device=dev)
+    yv = torch.empty(w.M, dtype=torch.complex64, device=dev)
+    xa = torch.empty(w.n, w.n, dtype=torch.complex64, device=dev)
+    reps = 50
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(float(k))
+        pe[k][0].record(stream)
+        ctx.phi(xr, out=yv)
+        ctx.phi_adj(yv, out=xa)
+        pe[k][1].record(stream)
+    torch.cuda.synchronize()
+    phi_ms = float(np.mean([a.elapsed_time(b) for a, b in pe]))
+    gvis = world * w.M / (phi_ms / 1e3) / 1e9
+
+    # --- end to end through the C ABI with host buffers -----------------
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty((w.n, w.n), dtype=torch.complex64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 100))
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        flush.fill_(float(k))
+        st.set_data(y_host)      # H2D of this step's data
+        one_step()
+        st.get_image(x_host)     # D2H of the step's result (synchronises)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    # the flush is inside this wall-clock region: take it out with its own timing
+    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+    for a, b in fl:
+        a.record(stream)
+        flush.fill_(1.0)
+        b.record(stream)
+    torch.cuda.synchronize()
+    flush_s = float(np.mean([a.elapsed_time(b) for a, b in fl])) / 1e3
+    e2e_value = world * e2e_steps / max(e2e_s - e2e_steps * flush_s, 1e-9)
+    clocks = sampler.stop()
+
+    # --- per-kernel times (profiled steps) and the roofline ---------------
+    ctx.profile_enable(True)
+    prof_steps = min(args.steps, 30)
+    for k in range(prof_steps):
+        flush.fill_(float(k))
+        one_step()
+    prof = ctx.profile_collect()
+    ctx.profile_enable(False)
+    dom = max(prof, key=lambda r: r[2])
+    abytes = algorithmic_bytes(w)
+    peak, peak_kind = peaks()
+    per_launch_s = dom[2] / dom[1] / 1e3
+    achieved = abytes.get(dom[0], float("nan")) / per_launch_s / 1e9
+    total_prof = sum(r[2] for r in prof)
+    kernels = {nm: {"launches": n_, "ms": round(ms, 4), "share": round(ms / total_prof, 4),
+                    "us_per_launch": round(ms / n_ * 1e3, 2),
+                    "alg_GBps": (round(abytes[nm] / (ms / n_ / 1e3) / 1e9, 1) if nm in abytes else None)}
+               for nm, n_, ms in prof}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**workload_config(w), "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "cuda_graph": True, "parallelism": f"{world} independent problems (one per GPU)"},
+            "phi_phiadj": {"value": gvis, "unit": "Gvis/s", "ms": phi_ms},
+            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "alg_bytes_per_launch": abytes.get(dom[0]),
+                         "us_per_launch": per_launch_s * 1e6},
+            "kernels": kernels,
+            "cpu_baseline": cpu_entry,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
+                    "d2h_bytes_per_step": 8 * w.n * w.n},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

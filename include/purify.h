@@ -175,10 +175,13 @@ typedef struct {
   double beta;        /* gamma = beta ||Psi^H Phi^H y||_inf; 1e-3 in §4.4 */
   double xi;          /* bound on the relative change of f1; 1e-3 */
   double tau;         /* tolerance on nu = ||y - Phi x||/eps; 0.1 */
+  int32_t use_graph;  /* 1: purify_sdmm_step replays one CUDA graph of the
+                         whole iteration (captured at its first call on a
+                         private stream); 0: launches kernel by kernel */
 } purify_sdmm_params;
 
 /* Defaults of §4.4: T = 300, k = 10, 1 round, no halting checks,
- * beta = xi = 1e-3, tau = 0.1. */
+ * beta = xi = 1e-3, tau = 0.1; use_graph = 1. */
 void purify_sdmm_default_params(purify_sdmm_params* p);
 
 /* Halting quantities after the last iteration (§4.4). */
@@ -256,6 +259,24 @@ int purify_sdmm_export(purify_ctx* ctx, purify_sdmm_state* st, void* host_buf,
                        size_t bytes, purify_stream_t stream);
 int purify_sdmm_import(purify_ctx* ctx, purify_sdmm_state* st, const void* host_buf,
                        size_t bytes, purify_stream_t stream);
+
+/* Kernel timing (measurement utility; the paper has no counterpart).
+ * purify_profile_enable(ctx, 1) makes every later kernel launch of this
+ * context record a CUDA event before and after it on its stream;
+ * purify_profile_collect synchronises the device, and for each kernel family
+ * (in order of first launch) writes its name (NUL-terminated, at most 31
+ * characters, into names + 32 * i), its number of launches and its total
+ * event-timed milliseconds; at most max_entries entries, the count in
+ * *n_entries.  Collecting clears the records; enable(ctx, 0) stops
+ * recording.  Events add a little launch overhead: time throughput with
+ * profiling off. */
+int purify_profile_enable(purify_ctx* ctx, int on);
+int purify_profile_collect(purify_ctx* ctx, int32_t max_entries, char* names,
+                           int64_t* launches, double* ms, int32_t* n_entries);
+
+/* Number of kernels the library has launched in this process (all
+ * contexts), counted on the host at each launch. */
+uint64_t purify_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -43,7 +43,7 @@ class Desc(ctypes.Structure):
 class SdmmParams(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("cg_iters", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("beta", ctypes.c_double), ("xi", ctypes.c_double),
-                ("tau", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("use_graph", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -87,6 +87,10 @@ _SIGS = {
     "purify_sdmm_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "purify_sdmm_export": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "purify_sdmm_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "purify_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "purify_profile_collect": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(_i32)]),
+    "purify_launch_count": (ctypes.c_uint64, []),
 }
 
 
@@ -264,6 +268,24 @@ class Context:
                self.lib.purify_cg_solve(self.ctx, _ptr(b), _ptr(x), int(iters), _ptr(res), _stream(stream)))
         return x, res
 
+    # kernel timing -------------------------------------------------------
+    def profile_enable(self, on: bool = True) -> None:
+        _check("purify_profile_enable", self.lib.purify_profile_enable(self.ctx, int(bool(on))))
+
+    def profile_collect(self, max_entries: int = 64) -> list[tuple[str, int, float]]:
+        """[(kernel, launches, total ms)] since the last collect (synchronises)."""
+        names = ctypes.create_string_buffer(32 * max_entries)
+        launches = (_i64 * max_entries)()
+        ms = (ctypes.c_double * max_entries)()
+        n = _i32()
+        _check("purify_profile_collect",
+               self.lib.purify_profile_collect(self.ctx, max_entries, names, launches, ms, ctypes.byref(n)))
+        out = []
+        for k in range(n.value):
+            nm = names.raw[32 * k: 32 * (k + 1)].split(b"\0", 1)[0].decode()
+            out.append((nm, int(launches[k]), float(ms[k])))
+        return out
+
     # SDMM ----------------------------------------------------------------
     def sdmm_state(self) -> "SdmmState":
         return SdmmState(self)
@@ -282,6 +304,11 @@ class Context:
                self.lib.purify_sdmm_solve(self.ctx, _ptr(y), float(eps), ctypes.byref(p), _ptr(out),
                                           ctypes.byref(rep), _stream(stream)))
         return out, rep.as_dict()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().purify_launch_count())
 
 
 def default_params() -> SdmmParams:
@@ -312,9 +339,10 @@ class SdmmState:
             pass
 
     def init(self, y, eps: float, cg_iters: int = 10, beta: float = 1e-3, max_iters: int = 300,
-             rounds: int = 1, stream=None) -> None:
+             rounds: int = 1, use_graph: bool = True, stream=None) -> None:
         p = default_params()
         p.cg_iters, p.beta, p.max_iters, p.rounds = cg_iters, beta, max_iters, rounds
+        p.use_graph = int(bool(use_graph))
         _check("purify_sdmm_init", self.lib.purify_sdmm_init(self.c.ctx, self.st, _ptr(y), float(eps),
                                                              ctypes.byref(p), _stream(stream)))
 

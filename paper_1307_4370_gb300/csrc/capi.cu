@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -14,6 +15,8 @@ using namespace purify;
 namespace purify {
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? PURIFY_OK : PURIFY_E_CUDA; }
+
+std::atomic<unsigned long long> g_launches{0};
 
 }  // namespace purify
 
@@ -210,6 +213,7 @@ void free_ctx(purify_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -223,7 +227,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   TRY(dev_alloc(&d_uv_user, M));
   if ((st = dev_alloc(&d_k0, M)) != PURIFY_OK) { cudaFree(d_uv_user); return st; }
   cudaMemcpyAsync(d_uv_user, uv_in, M * sizeof(float2), cudaMemcpyDefault, s);
-  k_footprint<<<nblk(M), 256, 0, s>>>(d_uv_user, M, c->ks, c->J, c->L, d_k0);
+  PURIFY_LAUNCH(c, "footprint", s, (k_footprint<<<nblk(M), 256, 0, s>>>(d_uv_user, M, c->ks, c->J, c->L, d_k0)));
   std::vector<int2> k0(M);
   cudaMemcpyAsync(k0.data(), d_k0, M * sizeof(int2), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -310,6 +314,48 @@ int load_data(purify_ctx* c, purify_sdmm_state* st, const float* y, cudaStream_t
   TRY_CUDA(cudaMemcpyAsync(c->d_vis2, y, M * sizeof(float2), cudaMemcpyDefault, s));
   TRY(launch_gather_perm(M, c->d_vis2, c->d_perm, st->y, s));
   st->y_bf16 = 0;
+  return PURIFY_OK;
+}
+
+// Algorithm 1 steps 5-9 for one iteration, enqueued on s.
+int enqueue_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
+  const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
+  // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r, p hold r0 = b - Q x_hat(t-1))
+  for (int k = 0; k < st->params.cg_iters; ++k) TRY(cg_step(c, st->xhat, st->r, st->p, st->qp, s));
+  // i = 2, first half: s2 = Phi x_hat and the l2 norms (FP64)
+  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{st->xhat, nullptr}, s));
+  DegridArgs da{};
+  da.out = st->s2;
+  da.z2 = st->z2;
+  da.y = st->y_bf16 ? nullptr : st->y;
+  da.yb = st->yb;
+  da.yscale = st->yscale;
+  TRY(degrid(c, kDegridSdmm, da, s));
+  // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
+  SaraProxArgs pa{st->z1, st->u1, st->w};
+  TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
+  // i = 2, second half: ball projection, z2 update, v = u2 - s2
+  TRY(launch_sdmm_l2_update(st, s));
+  // x1 = Psi u1
+  TRY(sara_synthesis(c, st->u1, st->x1, s));
+  // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual
+  TRY(grid_adjoint(c, kGridSorted, st->v, s));
+  RowOutArgs ra{};
+  ra.out = st->r;
+  ra.p = st->xhat;
+  ra.x1 = st->x1;
+  ra.z3 = st->z3;
+  ra.pdir = st->p;
+  TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s));
+  st->launches_per_step = (int)(g_launches.load(std::memory_order_relaxed) - l0);
+  return PURIFY_OK;
+}
+
+int drop_graph(purify_sdmm_state* st) {
+  if (st->step_exec) {
+    cudaGraphExecDestroy(st->step_exec);
+    st->step_exec = nullptr;
+  }
   return PURIFY_OK;
 }
 
@@ -480,7 +526,7 @@ int purify_proj_l2ball(purify_ctx* c, int64_t count, const float* in, const floa
   TRY(launch_l2_norm_diff(c, count, (const float2*)in, (const float2*)y, s));
   TRY(launch_l2_project(count, (const float2*)in, (const float2*)y, eps, &c->d_sc->norm2, (float2*)out, s));
   if (norm_out) {
-    k_sqrt_to<<<1, 1, 0, s>>>(&c->d_sc->norm2, norm_out);
+    PURIFY_LAUNCH(c, "sqrt", s, (k_sqrt_to<<<1, 1, 0, s>>>(&c->d_sc->norm2, norm_out)));
     TRY_CUDA(cudaGetLastError());
   }
   return PURIFY_OK;
@@ -531,12 +577,15 @@ void purify_sdmm_default_params(purify_sdmm_params* p) {
   p->beta = 1e-3;
   p->xi = 1e-3;
   p->tau = 0.1;
+  p->use_graph = 1;
 }
 
 void purify_sdmm_state_destroy(purify_sdmm_state* st) {
   if (!st) return;
   DeviceGuard g(st->ctx->device);
   cudaDeviceSynchronize();
+  drop_graph(st);
+  if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
   void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->x1, st->z3, st->z1, st->u1,
                   st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v};
   for (void* p : ptrs)
@@ -604,7 +653,7 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   TRY_CUDA(cudaMemsetAsync(st->z2, 0, M * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->s2, 0, M * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->v, 0, M * sizeof(float2), s));
-  k_fill_f32<<<nblk(D), 256, 0, s>>>(D, st->w, 1.0f);
+  PURIFY_LAUNCH(c, "fill", s, (k_fill_f32<<<nblk(D), 256, 0, s>>>(D, st->w, 1.0f)));
   TRY_CUDA(cudaGetLastError());
   // scalars: everything zero but eps
   DevScalars z{};
@@ -631,33 +680,33 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
   if (!c || !st || st->ctx != c) return PURIFY_E_INVALID_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r, p hold r0 = b - Q x_hat(t-1))
-  for (int k = 0; k < st->params.cg_iters; ++k) TRY(cg_step(c, st->xhat, st->r, st->p, st->qp, s));
-  // i = 2, first half: s2 = Phi x_hat and the l2 norms (FP64)
-  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{st->xhat, nullptr}, s));
-  DegridArgs da{};
-  da.out = st->s2;
-  da.z2 = st->z2;
-  da.y = st->y_bf16 ? nullptr : st->y;
-  da.yb = st->yb;
-  da.yscale = st->yscale;
-  TRY(degrid(c, kDegridSdmm, da, s));
-  // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
-  SaraProxArgs pa{st->z1, st->u1, st->w};
-  TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
-  // i = 2, second half: ball projection, z2 update, v = u2 - s2
-  TRY(launch_sdmm_l2_update(st, s));
-  // x1 = Psi u1
-  TRY(sara_synthesis(c, st->u1, st->x1, s));
-  // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual
-  TRY(grid_adjoint(c, kGridSorted, st->v, s));
-  RowOutArgs ra{};
-  ra.out = st->r;
-  ra.p = st->xhat;
-  ra.x1 = st->x1;
-  ra.z3 = st->z3;
-  ra.pdir = st->p;
-  TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s));
+  if (!st->params.use_graph || c->prof.on) {
+    TRY(enqueue_step(c, st, s));
+  } else {
+    const int key = st->params.cg_iters * 2 + st->y_bf16;
+    if (!st->step_exec || st->graph_cg_iters != key) {
+      TRY(drop_graph(st));
+      if (!st->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
+      TRY_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeRelaxed));
+      const int rc = enqueue_step(c, st, st->cap_stream);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(st->cap_stream, &graph);
+      if (rc != PURIFY_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != PURIFY_OK ? rc : PURIFY_E_CUDA;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&st->step_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        st->step_exec = nullptr;
+        return PURIFY_E_CUDA;
+      }
+      st->graph_cg_iters = key;
+    }
+    TRY_CUDA(cudaGraphLaunch(st->step_exec, s));
+    g_launches.fetch_add(st->launches_per_step, std::memory_order_relaxed);
+  }
   st->iters++;
   return PURIFY_OK;
 }
@@ -813,5 +862,51 @@ int purify_sdmm_import(purify_ctx* c, purify_sdmm_state* st, const void* host_bu
   st->y_bf16 = 0;
   return check_cuda(cudaStreamSynchronize(s));
 }
+
+int purify_profile_enable(purify_ctx* c, int on) {
+  if (!c) return PURIFY_E_INVALID_ARG;
+  c->prof.on = on != 0;
+  return PURIFY_OK;
+}
+
+int purify_profile_collect(purify_ctx* c, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                           int32_t* n_entries) {
+  if (!c || max_entries < 0 || !n_entries || (max_entries > 0 && (!names || !launches || !ms)))
+    return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  TRY_CUDA(cudaDeviceSynchronize());
+  std::vector<std::string> keys;
+  std::vector<int64_t> cnt;
+  std::vector<double> tot;
+  for (const auto& r : c->prof.recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->prof.pool[r.second], c->prof.pool[r.second + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    size_t k = 0;
+    while (k < keys.size() && keys[k] != r.first) ++k;
+    if (k == keys.size()) {
+      keys.emplace_back(r.first);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[k] += 1;
+    tot[k] += t;
+  }
+  const int ne = (int)std::min<size_t>(keys.size(), (size_t)max_entries);
+  for (int k = 0; k < ne; ++k) {
+    std::memset(names + 32 * k, 0, 32);
+    std::strncpy(names + 32 * k, keys[k].c_str(), 31);
+    launches[k] = cnt[k];
+    ms[k] = tot[k];
+  }
+  *n_entries = ne;
+  c->prof.recs.clear();
+  c->prof.used = 0;
+  return PURIFY_OK;
+}
+
+uint64_t purify_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -2,8 +2,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
+#include <utility>
+#include <vector>
 
 #include "purify.h"
 
@@ -126,6 +129,20 @@ struct DevScalars {
 
 constexpr int kMaxPartials = 32768;  // blocks per reduction (NV <= 2 values each)
 
+// ---------------------------------------------------------------------------
+// Kernel timing: when enabled on a context, every launch is bracketed by two
+// CUDA events on its stream; collect() aggregates the durations per kernel.
+// A process-wide counter counts every kernel launch of the library.
+// ---------------------------------------------------------------------------
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<const char*, size_t>> recs;  // kernel name, index of its start event
+};
+
+extern std::atomic<unsigned long long> g_launches;
+
 }  // namespace purify
 
 // ---------------------------------------------------------------------------
@@ -167,7 +184,42 @@ struct purify_ctx {
   double* d_partials;   // kNumCounters x kMaxPartials
   purify::DevScalars* d_sc;
   purify::DevScalars* h_sc;  // pinned host mirror
+
+  purify::Profiler prof;
 };
+
+namespace purify {
+
+// Bracket one kernel launch (see Profiler).
+inline size_t prof_start(purify_ctx* c, cudaStream_t s) {
+  if (!c || !c->prof.on) return (size_t)-1;
+  while (c->prof.pool.size() < c->prof.used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    c->prof.pool.push_back(e);
+  }
+  const size_t i = c->prof.used;
+  cudaEventRecord(c->prof.pool[i], s);
+  c->prof.used += 2;
+  return i;
+}
+
+inline void prof_stop(purify_ctx* c, const char* name, cudaStream_t s, size_t i) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (i == (size_t)-1) return;
+  cudaEventRecord(c->prof.pool[i + 1], s);
+  c->prof.recs.emplace_back(name, i);
+}
+
+}  // namespace purify
+
+// Launch statement `stmt` (a kernel launch) under the profiler.
+#define PURIFY_LAUNCH(ctx, name, stream, stmt)                \
+  do {                                                        \
+    const size_t _pi = purify::prof_start((ctx), (stream));   \
+    stmt;                                                     \
+    purify::prof_stop((ctx), (name), (stream), _pi);          \
+  } while (0)
 
 struct purify_sdmm_state {
   purify_ctx* ctx;
@@ -193,6 +245,11 @@ struct purify_sdmm_state {
   double eps;
   int64_t iters;
   purify_sdmm_params params;
+  // CUDA graph of one SDMM step (captured on a private stream, replayed on the caller's)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t step_exec;
+  int graph_cg_iters;       // key of the captured graph (cg_iters, data format)
+  int launches_per_step;    // kernels in one captured step
 };
 
 namespace purify {

@@ -353,9 +353,10 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
   const size_t smr = (size_t)rs.nsig * c->L * sizeof(float2);
   const size_t smc = (size_t)cs.nsig * c->L * sizeof(float2);
   const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
-#define ROWF(E, MD)                                                                               \
-  k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan, c->n, \
-                                               rs.nsig, c->d_sc)
+#define ROWF(E, MD)                                                                                        \
+  PURIFY_LAUNCH(c, "row_fwd", s,                                                                           \
+                (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan, c->n, \
+                                                              rs.nsig, c->d_sc)))
   if (rs.ept == 8) {
     if (mode == kRowInPlain) ROWF(8, kRowInPlain); else ROWF(8, kRowInCgDir);
   } else {
@@ -364,10 +365,12 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
 #undef ROWF
   if (cs.ept == 8) {
     allow_smem(k_col_fwd<8>, smc);
-    k_col_fwd<8><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig);
+    PURIFY_LAUNCH(c, "col_fwd", s,
+                  (k_col_fwd<8><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig)));
   } else {
     allow_smem(k_col_fwd<12>, smc);
-    k_col_fwd<12><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig);
+    PURIFY_LAUNCH(c, "col_fwd", s,
+                  (k_col_fwd<12><<<gc, cs.threads, smc, s>>>(c->d_half, c->d_grid, c->d_tw, c->plan, c->n, cs.nsig)));
   }
   return check_cuda(cudaGetLastError());
 }
@@ -377,9 +380,10 @@ static void degrid_J(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStr
   const int threads = 256;
   int64_t blocks = (c->M + threads - 1) / threads;
   if (blocks > kMaxPartials) blocks = kMaxPartials;
-#define DEG(MD)                                                                                  \
-  k_degrid<J, MD><<<(unsigned)blocks, threads, 0, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->kb, \
-                                                       c->ks, c->L, c->M, c->d_partials, c->d_sc)
+#define DEG(MD)                                                                                              \
+  PURIFY_LAUNCH(c, "degrid", s,                                                                              \
+                (k_degrid<J, MD><<<(unsigned)blocks, threads, 0, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->kb, \
+                                                                      c->ks, c->L, c->M, c->d_partials, c->d_sc)))
   if (mode == kDegridPerm) DEG(kDegridPerm);
   else if (mode == kDegridSorted) DEG(kDegridSorted);
   else DEG(kDegridSdmm);
@@ -401,13 +405,16 @@ static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s
   const int threads = 256;
   const size_t sm = 2 * (size_t)c->tileT * c->tileT * sizeof(float);
   if (mode == kGridPerm)
-    k_grid<J, kGridPerm><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
-                                                         c->d_tile_list, c->d_tile_order, c->kb, c->ks, c->L,
-                                                         c->tileT, c->tiles_1d);
+    PURIFY_LAUNCH(c, "grid", s,
+                  (k_grid<J, kGridPerm><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
+                                                                       c->d_tile_list, c->d_tile_order, c->kb, c->ks,
+                                                                       c->L, c->tileT, c->tiles_1d)));
   else
-    k_grid<J, kGridSorted><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
-                                                           c->d_tile_list, c->d_tile_order, c->kb, c->ks, c->L,
-                                                           c->tileT, c->tiles_1d);
+    PURIFY_LAUNCH(c, "grid", s,
+                  (k_grid<J, kGridSorted><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis,
+                                                                         c->d_tile_off, c->d_tile_list,
+                                                                         c->d_tile_order, c->kb, c->ks, c->L,
+                                                                         c->tileT, c->tiles_1d)));
 }
 
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
@@ -427,14 +434,17 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
   const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
   if (cs.ept == 8) {
     allow_smem(k_col_inv<8>, smc);
-    k_col_inv<8><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig);
+    PURIFY_LAUNCH(c, "col_inv", s,
+                  (k_col_inv<8><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
   } else {
     allow_smem(k_col_inv<12>, smc);
-    k_col_inv<12><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig);
+    PURIFY_LAUNCH(c, "col_inv", s,
+                  (k_col_inv<12><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
   }
-#define ROWI(E, MD)                                                                                     \
-  k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan, c->n, rs.nsig, \
-                                               c->d_partials, c->d_sc)
+#define ROWI(E, MD)                                                                                          \
+  PURIFY_LAUNCH(c, "row_inv", s,                                                                             \
+                (k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan, c->n, \
+                                                              rs.nsig, c->d_partials, c->d_sc)))
   if (rs.ept == 8) {
     if (mode == kRowOutPlain) ROWI(8, kRowOutPlain);
     else if (mode == kRowOutCgQ) ROWI(8, kRowOutCgQ);

@@ -340,17 +340,17 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
   if (dirac_plane >= 0) {
     int blocks = (int)std::min<int64_t>((N + 255) / 256, 1024);
     if (mode == kSaraPlain)
-      k_dirac<kSaraPlain><<<blocks, 256, 0, s>>>(x, alpha + (size_t)dirac_plane * N, N, scale, pa,
-                                                 c->d_partials, c->d_sc);
-    else {
-      SaraProxArgs pd = pa;  // prox arrays are indexed over the whole coefficient vector
-      k_dirac<kSaraProx><<<blocks, 256, 0, s>>>(x, nullptr, N, scale, pd, c->d_partials, c->d_sc);
-    }
+      PURIFY_LAUNCH(c, "dirac", s,
+                    (k_dirac<kSaraPlain><<<blocks, 256, 0, s>>>(x, alpha + (size_t)dirac_plane * N, N, scale, pa,
+                                                                c->d_partials, c->d_sc)));
+    else
+      PURIFY_LAUNCH(c, "dirac", s,
+                    (k_dirac<kSaraProx><<<blocks, 256, 0, s>>>(x, nullptr, N, scale, pa, c->d_partials, c->d_sc)));
   } else if (mode == kSaraProx) {
     cudaMemsetAsync(&c->d_sc->f1, 0, sizeof(double), s);
   }
   if (nb == 0) {
-    if (mode == kSaraProx) k_finish_zeta<<<1, 1, 0, s>>>(c->d_sc);
+    if (mode == kSaraProx) PURIFY_LAUNCH(c, "finish_zeta", s, (k_finish_zeta<<<1, 1, 0, s>>>(c->d_sc)));
     return check_cuda(cudaGetLastError());
   }
   int maxp = 1;
@@ -365,11 +365,13 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
     dim3 grid(H / TI, H / TI, nb);
     const size_t sm = dwt_smem(TI, 2 * maxp);
     if (mode == kSaraPlain)
-      k_dwt_level<kSaraPlain><<<grid, 256, sm, s>>>(in, lev == 0, llo, alpha, G, bl, c->wf, pa, c->d_partials,
-                                                     c->d_sc);
+      PURIFY_LAUNCH(c, "dwt_level", s,
+                    (k_dwt_level<kSaraPlain><<<grid, 256, sm, s>>>(in, lev == 0, llo, alpha, G, bl, c->wf, pa,
+                                                                   c->d_partials, c->d_sc)));
     else
-      k_dwt_level<kSaraProx><<<grid, 256, sm, s>>>(in, lev == 0, llo, pa.z1, G, bl, c->wf, pa, c->d_partials,
-                                                    c->d_sc);
+      PURIFY_LAUNCH(c, "dwt_level", s,
+                    (k_dwt_level<kSaraProx><<<grid, 256, sm, s>>>(in, lev == 0, llo, pa.z1, G, bl, c->wf, pa,
+                                                                  c->d_partials, c->d_sc)));
   }
   return check_cuda(cudaGetLastError());
 }
@@ -382,7 +384,7 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
   const float scale = 1.0f / sqrtf((float)c->q);
   if (nb == 0) {
     int blocks = (int)std::min<int64_t>((N + 255) / 256, 1024);
-    k_dirac_syn<<<blocks, 256, 0, s>>>(alpha + (size_t)dirac_plane * N, x, N, scale);
+    PURIFY_LAUNCH(c, "dirac", s, (k_dirac_syn<<<blocks, 256, 0, s>>>(alpha + (size_t)dirac_plane * N, x, N, scale)));
     return check_cuda(cudaGetLastError());
   }
   int maxp = 1;
@@ -397,7 +399,8 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
     float2* llo = c->d_ll[lev & 1];
     dim3 grid(L / (2 * TO), L / (2 * TO), lev == 0 ? 1 : nb);
     const size_t sm = idwt_smem(TO, maxp);
-    k_idwt_level<<<grid, 256, sm, s>>>(llin, from_plane, llo, alpha, x, dirac_plane, G, bl, c->wf);
+    PURIFY_LAUNCH(c, "idwt_level", s,
+                  (k_idwt_level<<<grid, 256, sm, s>>>(llin, from_plane, llo, alpha, x, dirac_plane, G, bl, c->wf)));
   }
   return check_cuda(cudaGetLastError());
 }

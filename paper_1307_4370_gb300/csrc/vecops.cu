@@ -191,69 +191,69 @@ __global__ void k_set_gamma(DevScalars* sc, double beta) { sc->gamma = beta * sc
 // ---------------------------------------------------------------------------
 int launch_soft_threshold(int64_t count, const float2* in, const float* w, const double* gamma_dev, float gamma,
                           float2* out, cudaStream_t s) {
-  k_soft<<<blocks_for(count), 256, 0, s>>>(count, in, w, gamma_dev, gamma, out);
+  PURIFY_LAUNCH(nullptr, "soft", s, (k_soft<<<blocks_for(count), 256, 0, s>>>(count, in, w, gamma_dev, gamma, out)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_l2_norm_diff(purify_ctx* c, int64_t count, const float2* a, const float2* b, cudaStream_t s) {
-  k_norm_diff<<<blocks_for(count), 256, 0, s>>>(count, a, b, c->d_partials, c->d_sc);
+  PURIFY_LAUNCH(c, "norm_diff", s, (k_norm_diff<<<blocks_for(count), 256, 0, s>>>(count, a, b, c->d_partials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_l2_project(int64_t count, const float2* in, const float2* y, double eps, const double* norm2_dev,
                       float2* out, cudaStream_t s) {
-  k_l2_project<<<blocks_for(count), 256, 0, s>>>(count, in, y, eps, norm2_dev, out);
+  PURIFY_LAUNCH(nullptr, "l2_project", s, (k_l2_project<<<blocks_for(count), 256, 0, s>>>(count, in, y, eps, norm2_dev, out)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s) {
-  k_positive<<<blocks_for(count), 256, 0, s>>>(count, in, out);
+  PURIFY_LAUNCH(nullptr, "positive", s, (k_positive<<<blocks_for(count), 256, 0, s>>>(count, in, out)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_cg_update(purify_ctx* c, float2* x, float2* r, const float2* p, const float2* qp, cudaStream_t s) {
   const int64_t N = (int64_t)c->n * c->n;
-  k_cg_update<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, qp, c->d_partials, c->d_sc);
+  PURIFY_LAUNCH(c, "cg_update", s, (k_cg_update<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, qp, c->d_partials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, float2* p,
                             cudaStream_t s) {
   const int64_t N = (int64_t)c->n * c->n;
-  k_cg_residual_init<<<blocks_for(N), 256, 0, s>>>(N, b, qx, r, p, c->d_partials, c->d_sc);
+  PURIFY_LAUNCH(c, "cg_residual_init", s, (k_cg_residual_init<<<blocks_for(N), 256, 0, s>>>(N, b, qx, r, p, c->d_partials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s) {
-  k_max_abs<<<blocks_for(count), 256, 0, s>>>(count, a, c->d_partials, c->d_sc);
+  PURIFY_LAUNCH(c, "max_abs", s, (k_max_abs<<<blocks_for(count), 256, 0, s>>>(count, a, c->d_partials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s) {
   purify_ctx* c = st->ctx;
-  k_sdmm_l2<<<blocks_for(c->M), 256, 0, s>>>(c->M, st->s2, st->z2, st->y_bf16 ? nullptr : st->y, st->yb,
-                                             st->yscale, st->v, c->d_sc);
+  PURIFY_LAUNCH(st->ctx, "sdmm_l2", s, (k_sdmm_l2<<<blocks_for(c->M), 256, 0, s>>>(c->M, st->s2, st->z2, st->y_bf16 ? nullptr : st->y, st->yb,
+                                             st->yscale, st->v, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round, cudaStream_t s) {
-  k_reweight<<<blocks_for(count), 256, 0, s>>>(count, alpha, w, round, c->d_sc);
+  PURIFY_LAUNCH(c, "reweight", s, (k_reweight<<<blocks_for(count), 256, 0, s>>>(count, alpha, w, round, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_gather_perm(int64_t M, const float2* src, const int* perm, float2* dst, cudaStream_t s) {
-  k_gather<<<blocks_for(M), 256, 0, s>>>(M, src, perm, dst);
+  PURIFY_LAUNCH(nullptr, "gather", s, (k_gather<<<blocks_for(M), 256, 0, s>>>(M, src, perm, dst)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_quantize_bf16(int64_t M, const float2* y, uint16_t* yb, float* yscale, cudaStream_t s) {
   const int64_t blocks = (M + 4095) / 4096;
-  k_quantize_bf16<<<(unsigned)blocks, 256, 0, s>>>(M, y, reinterpret_cast<uint32_t*>(yb), yscale);
+  PURIFY_LAUNCH(nullptr, "quantize_bf16", s, (k_quantize_bf16<<<(unsigned)blocks, 256, 0, s>>>(M, y, reinterpret_cast<uint32_t*>(yb), yscale)));
   return check_cuda(cudaGetLastError());
 }
 
 int launch_set_gamma(purify_ctx* c, double beta, cudaStream_t s) {
-  k_set_gamma<<<1, 1, 0, s>>>(c->d_sc, beta);
+  PURIFY_LAUNCH(c, "set_gamma", s, (k_set_gamma<<<1, 1, 0, s>>>(c->d_sc, beta)));
   return check_cuda(cudaGetLastError());
 }
 

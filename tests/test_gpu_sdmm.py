@@ -134,3 +134,48 @@ def test_bf16_data_close_to_fp32():
     s32 = simulate.snr_db(p.x_true, xs["fp32"].real)
     s16 = simulate.snr_db(p.x_true, xs["bf16"].real)
     assert abs(s32 - s16) <= 0.1
+
+
+def test_graph_replay_matches_eager_launches():
+    """The CUDA-graph replay of a step and the kernel-by-kernel launches give the same iterates."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p, y, eps = problem("sdmm64")
+    w = p.workload
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    xs = []
+    for use_graph in (True, False):
+        st = ctx.sdmm_state()
+        st.init(dev(y, torch), eps, use_graph=use_graph)
+        for _ in range(12):
+            st.step()
+        st.reweight(1)
+        for _ in range(3):
+            st.step()
+        xs.append(host(st.get_image()))
+    assert rel_err(xs[0], xs[1]) <= 1e-6
+
+
+def test_profiler_and_launch_counter():
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p, y, eps = problem("sdmm64")
+    w = p.workload
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    st = ctx.sdmm_state()
+    st.init(dev(y, torch), eps)
+    st.step()  # captures the graph
+    l0 = binding.launch_count()
+    st.step()
+    per_step = binding.launch_count() - l0
+    ctx.profile_enable(True)
+    st.step()
+    prof = ctx.profile_collect()
+    ctx.profile_enable(False)
+    names = {r[0] for r in prof}
+    assert {"row_fwd", "col_fwd", "degrid", "grid", "col_inv", "row_inv", "cg_update", "dwt_level",
+            "idwt_level", "sdmm_l2"} <= names
+    assert sum(r[1] for r in prof) == per_step
+    assert all(r[2] > 0 for r in prof)
