@@ -108,42 +108,38 @@ void solve_dense(std::vector<long double>& A, std::vector<long double>& b, int n
 }
 
 // Fit each tap's weight, as a function of z = 2x - 1 on [-1, 1], by the
-// polynomial interpolating it at Chebyshev nodes; take the lowest degree
-// whose float Horner evaluation is within 1.5e-7 of the double kernel.
+// degree-kKbDeg polynomial interpolating it at Chebyshev nodes (long double),
+// and record the largest error of its float Horner evaluation.
 KbPoly fit_kb(int J) {
   const double beta = kb_beta(J);
   const double i0b = std::cyl_bessel_i(0.0, beta);
   KbPoly kb{};
   kb.J = J;
-  for (int deg = 6; deg <= kMaxKbDeg; ++deg) {
-    const int np = deg + 1;
-    float err = 0.f;
-    for (int a = 0; a < J; ++a) {
-      std::vector<long double> A(np * np), f(np);
-      for (int i = 0; i < np; ++i) {
-        const long double z = std::cos(M_PI * (i + 0.5) / np);
-        const double x = 0.5 * ((double)z + 1.0);
-        long double zp = 1.0L;
-        for (int j = 0; j < np; ++j) {
-          A[i * np + j] = zp;
-          zp *= z;
-        }
-        f[i] = kb_g(x + J / 2 - 1 - a, J, beta, i0b);
+  const int np = kKbDeg + 1;
+  float err = 0.f;
+  for (int a = 0; a < J; ++a) {
+    std::vector<long double> A(np * np), f(np);
+    for (int i = 0; i < np; ++i) {
+      const long double z = std::cos(M_PI * (i + 0.5) / np);
+      const double x = 0.5 * ((double)z + 1.0);
+      long double zp = 1.0L;
+      for (int j = 0; j < np; ++j) {
+        A[i * np + j] = zp;
+        zp *= z;
       }
-      solve_dense(A, f, np);
-      for (int j = 0; j < np; ++j) kb.c[a][j] = (float)f[j];
-      for (int t = 0; t <= 4000; ++t) {
-        const double x = t / 4000.0 * (1.0 - 1e-12);
-        const float z = std::fma(2.0f, (float)x, -1.0f);
-        float acc = kb.c[a][deg];
-        for (int k = deg - 1; k >= 0; --k) acc = std::fma(acc, z, kb.c[a][k]);
-        err = std::max(err, (float)std::fabs(acc - kb_g(x + J / 2 - 1 - a, J, beta, i0b)));
-      }
+      f[i] = kb_g(x + J / 2 - 1 - a, J, beta, i0b);
     }
-    kb.deg = deg;
-    kb.max_err = err;
-    if (err <= 1.5e-7f) break;
+    solve_dense(A, f, np);
+    for (int j = 0; j < np; ++j) kb.c[a][j] = (float)f[j];
+    for (int t = 0; t <= 4000; ++t) {
+      const double x = t / 4000.0 * (1.0 - 1e-12);
+      const float z = std::fma(2.0f, (float)x, -1.0f);
+      float acc = kb.c[a][kKbDeg];
+      for (int k = kKbDeg - 1; k >= 0; --k) acc = std::fma(acc, z, kb.c[a][k]);
+      err = std::max(err, (float)std::fabs(acc - kb_g(x + J / 2 - 1 - a, J, beta, i0b)));
+    }
   }
+  kb.max_err = err;
   return kb;
 }
 
@@ -207,7 +203,8 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_off, c->d_tile_list, c->d_tile_order,
+  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_list, c->d_chunks, c->d_tile_slot0,
+                  c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
   for (void* p : ptrs)
@@ -271,18 +268,40 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       for (int k = 0; k < nt; ++k) list[pos[tl[k]]++] = (int)si;
     }
   }
-  std::vector<int> order(c->ntiles);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return lcnt[a + 1] - lcnt[a] > lcnt[b + 1] - lcnt[b]; });
+  // work units: each tile's list in chunks of at most chunk_max entries
+  const int64_t mean = (c->nlist + c->ntiles - 1) / c->ntiles;
+  c->chunk_max = (int)std::max<int64_t>(256, ((2 * mean + 255) / 256) * 256);
+  std::vector<int4> chunks;
+  std::vector<int> slot0(c->ntiles, -1), nchunk(c->ntiles, 0);
+  int nslots = 0;
+  for (int t = 0; t < c->ntiles; ++t) {
+    const int b = lcnt[t], e = lcnt[t + 1];
+    const int nc = std::max(1, (e - b + c->chunk_max - 1) / c->chunk_max);
+    nchunk[t] = nc;
+    if (nc > 1) slot0[t] = nslots;
+    for (int k = 0; k < nc; ++k) {
+      const int cb = b + (int)((int64_t)(e - b) * k / nc), ce = b + (int)((int64_t)(e - b) * (k + 1) / nc);
+      chunks.push_back(make_int4(t, cb, ce, nc > 1 ? nslots + k : -1));
+    }
+    if (nc > 1) nslots += nc;
+  }
+  // heavy chunks first
+  std::stable_sort(chunks.begin(), chunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  c->nchunks = (int)chunks.size();
+  c->nslots = nslots;
   if ((st = dev_alloc(&c->d_uv, M)) == PURIFY_OK && (st = dev_alloc(&c->d_perm, M)) == PURIFY_OK &&
-      (st = dev_alloc(&c->d_tile_off, c->ntiles + 1)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_list, c->nlist)) == PURIFY_OK &&
-      (st = dev_alloc(&c->d_tile_order, c->ntiles)) == PURIFY_OK) {
+      (st = dev_alloc(&c->d_chunks, c->nchunks)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_slot0, c->ntiles)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_nchunk, c->ntiles)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_tile_cnt, c->ntiles)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_slots, (size_t)std::max(1, nslots) * T * T)) == PURIFY_OK) {
     cudaMemcpyAsync(c->d_perm, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_tile_off, lcnt.data(), (c->ntiles + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_list, list.data(), c->nlist * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_tile_order, order.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_chunks, chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_slot0, slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_nchunk, nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c->d_tile_cnt, 0, c->ntiles * sizeof(unsigned), s);
     launch_gather_perm(M, d_uv_user, c->d_perm, c->d_uv, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
   }
@@ -411,7 +430,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   c->plan = make_plan(c->L);
   if (c->plan.nst < 0) { delete c; return PURIFY_E_UNSUPPORTED; }
   make_daubechies(c->wf);
-  c->tileT = c->L >= 1024 ? 32 : (c->L >= 128 ? 16 : 8);
+  c->tileT = c->L >= 512 ? 32 : (c->L >= 64 ? 16 : 8);
   while (c->tileT < c->J || c->L % c->tileT) c->tileT *= 2;
   c->tiles_1d = c->L / c->tileT;
   c->ntiles = c->tiles_1d * c->tiles_1d;

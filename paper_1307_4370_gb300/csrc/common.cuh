@@ -33,12 +33,11 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 // monomials) so the device evaluates J weights by Horner.
 // ---------------------------------------------------------------------------
 constexpr int kMaxJ = 8;
-constexpr int kMaxKbDeg = 15;
+constexpr int kKbDeg = 8;  // degree of every tap polynomial (fit error <= 1.5e-7 for J <= 8)
 struct KbPoly {
   int J;
-  int deg;                         // polynomial degree (<= kMaxKbDeg)
-  float c[kMaxJ][kMaxKbDeg + 1];   // c[a][k]: coefficient of z^k for tap a
-  float max_err;                   // max abs fit error measured on the host
+  float c[kMaxJ][kKbDeg + 1];   // c[a][k]: coefficient of z^k for tap a
+  float max_err;                // max abs fit error measured on the host
 };
 
 // Error-free splitting of kappa = u * (2n / (2 pi)) into floor and fraction
@@ -65,8 +64,9 @@ __device__ __forceinline__ void kb_weights(const KbPoly& kb, float x, float* w) 
   const float z = fmaf(2.0f, x, -1.0f);
 #pragma unroll
   for (int a = 0; a < J; ++a) {
-    float acc = kb.c[a][kb.deg];
-    for (int k = kb.deg - 1; k >= 0; --k) acc = fmaf(acc, z, kb.c[a][k]);
+    float acc = kb.c[a][kKbDeg];
+#pragma unroll
+    for (int k = kKbDeg - 1; k >= 0; --k) acc = fmaf(acc, z, kb.c[a][k]);
     w[a] = acc;
   }
 }
@@ -169,10 +169,18 @@ struct purify_ctx {
   int tileT;            // tile side (cells)
   int tiles_1d;         // L / tileT
   int ntiles;
-  int* d_tile_off;      // ntiles + 1 offsets into d_tile_list
-  int* d_tile_list;     // sorted visibility indices whose footprint meets the tile
-  int* d_tile_order;    // tiles by decreasing list length
+  int* d_tile_list;     // sorted visibility indices whose footprint meets each tile, tile by tile
   int64_t nlist;
+  // gridding work units: each tile's list cut into chunks of at most chunk_max entries;
+  // a tile with several chunks sums their partial tiles (slots) in chunk order
+  int nchunks;
+  int chunk_max;
+  int4* d_chunks;       // (tile, begin, end, slot or -1)
+  int* d_tile_slot0;    // first slot of a multi-chunk tile
+  int* d_tile_nchunk;   // chunks per tile
+  unsigned* d_tile_cnt; // arrival counters (zero between launches)
+  int nslots;
+  float2* d_slots;      // nslots x tileT^2 partial tiles
 
   // scratch
   float2* d_grid;       // L x L

@@ -32,7 +32,7 @@ static FftShape row_shape(const purify_ctx* c) {
   FftShape f;
   f.ept = pick_ept(c->L);
   int nsig = 1;
-  while (nsig * 2 * c->L / f.ept <= 256 && c->n % (nsig * 2) == 0) nsig *= 2;
+  while (nsig * 2 * c->L / f.ept <= 128 && c->n % (nsig * 2) == 0) nsig *= 2;
   f.nsig = nsig;
   f.threads = nsig * c->L / f.ept;
   return f;
@@ -194,27 +194,33 @@ __global__ void k_degrid(const float2* __restrict__ X, const float2* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Gridding G^T: one CTA per output tile (T x T cells), in decreasing order of
-// work.  Visibilities whose footprint meets the tile are listed at set-up;
-// their contributions to cells inside the tile are summed in shared memory,
-// and the tile is written to X once.
+// Gridding G^T.  The grid is cut into T x T tiles; set-up listed, per tile,
+// the visibilities whose footprint meets it and cut each list into chunks of
+// at most chunk_max entries.  One CTA per chunk sums the contributions that
+// fall inside its tile in shared memory.  A tile with one chunk is written to
+// X directly; otherwise each chunk stores a partial tile and the last chunk
+// to finish adds the partials in chunk order and writes the tile, so every
+// grid cell is written exactly once and no global atomics touch the data.
 // ---------------------------------------------------------------------------
 template <int J, int MODE>
-__global__ void k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
-                       const int* __restrict__ perm, const float2* __restrict__ vis,
-                       const int* __restrict__ tile_off, const int* __restrict__ tile_list,
-                       const int* __restrict__ tile_order, KbPoly kb, KappaScale ks, int L, int T,
-                       int tiles_1d) {
+__global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
+                                              const int* __restrict__ perm, const float2* __restrict__ vis,
+                                              const int* __restrict__ tile_list, const int4* __restrict__ chunks,
+                                              const int* __restrict__ tile_slot0, const int* __restrict__ tile_nchunk,
+                                              unsigned* __restrict__ tile_cnt, float2* __restrict__ slots, KbPoly kb,
+                                              KappaScale ks, int L, int T, int tiles_1d) {
   extern __shared__ float smf[];
+  __shared__ bool s_last;
   float* accr = smf;
   float* acci = smf + T * T;
-  const int tile = tile_order[blockIdx.x];
+  const int4 ch = chunks[blockIdx.x];
+  const int tile = ch.x;
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
-  for (int k = threadIdx.x; k < T * T; k += blockDim.x) { accr[k] = 0.f; acci[k] = 0.f; }
+  const int TT = T * T;
+  for (int k = threadIdx.x; k < TT; k += blockDim.x) { accr[k] = 0.f; acci[k] = 0.f; }
   __syncthreads();
-  const int beg = tile_off[tile], end = tile_off[tile + 1];
-  for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+  for (int e = ch.y + threadIdx.x; e < ch.z; e += blockDim.x) {
     const int i = tile_list[e];
     const float2 u = __ldg(&uv[i]);
     const float2 val = (MODE == kGridPerm) ? __ldg(&vis[perm[i]]) : __ldg(&vis[i]);
@@ -234,23 +240,42 @@ __global__ void k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
       int rr = dr + aa;
       if (rr >= L) rr -= L;
       if (rr >= T) continue;
-      const float vr = wr[aa];
+      const float2 vr = make_float2(wr[aa] * val.x, wr[aa] * val.y);
 #pragma unroll
       for (int b = 0; b < J; ++b) {
         int cc = dc + b;
         if (cc >= L) cc -= L;
         if (cc >= T) continue;
-        const float w = vr * wc[b];
-        atomicAdd(&accr[rr * T + cc], w * val.x);
-        atomicAdd(&acci[rr * T + cc], w * val.y);
+        atomicAdd(&accr[rr * T + cc], wc[b] * vr.x);
+        atomicAdd(&acci[rr * T + cc], wc[b] * vr.y);
       }
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-    const int rr = k / T, cc = k - rr * T;
-    X[(size_t)(R0 + rr) * L + C0 + cc] = make_float2(accr[k], acci[k]);
+  if (ch.w < 0) {
+    for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+      const int rr = k / T, cc = k - rr * T;
+      X[(size_t)(R0 + rr) * L + C0 + cc] = make_float2(accr[k], acci[k]);
+    }
+    return;
   }
+  float2* mine = slots + (size_t)ch.w * TT;
+  for (int k = threadIdx.x; k < TT; k += blockDim.x) mine[k] = make_float2(accr[k], acci[k]);
+  __threadfence();
+  __syncthreads();
+  const int nc = tile_nchunk[tile];
+  if (threadIdx.x == 0) s_last = (atomicAdd(&tile_cnt[tile], 1u) == (unsigned)(nc - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const float2* first = slots + (size_t)tile_slot0[tile] * TT;
+  for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+    float2 sum = make_float2(0.f, 0.f);
+    for (int j = 0; j < nc; ++j) sum = cadd(sum, __ldcg(&first[(size_t)j * TT + k]));
+    const int rr = k / T, cc = k - rr * T;
+    X[(size_t)(R0 + rr) * L + C0 + cc] = sum;
+  }
+  if (threadIdx.x == 0) tile_cnt[tile] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -404,17 +429,15 @@ template <int J>
 static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
   const int threads = 256;
   const size_t sm = 2 * (size_t)c->tileT * c->tileT * sizeof(float);
-  if (mode == kGridPerm)
-    PURIFY_LAUNCH(c, "grid", s,
-                  (k_grid<J, kGridPerm><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_off,
-                                                                       c->d_tile_list, c->d_tile_order, c->kb, c->ks,
-                                                                       c->L, c->tileT, c->tiles_1d)));
-  else
-    PURIFY_LAUNCH(c, "grid", s,
-                  (k_grid<J, kGridSorted><<<c->ntiles, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis,
-                                                                         c->d_tile_off, c->d_tile_list,
-                                                                         c->d_tile_order, c->kb, c->ks, c->L,
-                                                                         c->tileT, c->tiles_1d)));
+#define GRD(MD)                                                                                             \
+  PURIFY_LAUNCH(c, "grid", s,                                                                               \
+                (k_grid<J, MD><<<c->nchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_list, \
+                                                               c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
+                                                               c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L,       \
+                                                               c->tileT, c->tiles_1d)))
+  if (mode == kGridPerm) GRD(kGridPerm);
+  else GRD(kGridSorted);
+#undef GRD
 }
 
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
