@@ -203,7 +203,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_list, c->d_chunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -268,9 +268,36 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       for (int k = 0; k < nt; ++k) list[pos[tl[k]]++] = (int)si;
     }
   }
-  // work units: each tile's list in chunks of at most chunk_max entries
+  // order each tile's list by the footprint start cell relative to the tile
+  // (key = (dr + J - 1) * W + (dc + J - 1), W = T + J - 1): the gridding
+  // kernel finds the visibilities starting at a given cell as one run
+  const int W = T + J - 1;
+  auto rel = [&](int k, int origin) {  // start offset in [-(J-1), L - J + 1)
+    int t = (k - origin) % L;
+    if (t < 0) t += L;
+    return t >= L - (J - 1) ? t - L : t;
+  };
+  {
+    std::vector<std::pair<int, int>> seg;
+    for (int t = 0; t < c->ntiles; ++t) {
+      const int R0 = (t / TD) * T, C0 = (t % TD) * T;
+      seg.clear();
+      for (int e = lcnt[t]; e < lcnt[t + 1]; ++e) {
+        const int2 k = k0[perm[list[e]]];
+        const int key = (rel(k.x, R0) + J - 1) * W + (rel(k.y, C0) + J - 1);
+        seg.emplace_back(key, list[e]);
+      }
+      std::stable_sort(seg.begin(), seg.end(),
+                       [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+      for (size_t k = 0; k < seg.size(); ++k) list[lcnt[t] + k] = seg[k].second;
+    }
+  }
+  // gridding work units: each tile's list in chunks that fit the kernel's
+  // shared memory (64 KB: start-cell offsets + key, value, 2J weights per entry)
   const int64_t mean = (c->nlist + c->ntiles - 1) / c->ntiles;
-  c->chunk_max = (int)std::max<int64_t>(256, ((2 * mean + 255) / 256) * 256);
+  const int per_entry = 12 + 8 * J;
+  const int cap = std::max(128, ((65536 - (W * W + 1) * 4) / per_entry) / 128 * 128);
+  c->chunk_max = (int)std::min<int64_t>(cap, std::max<int64_t>(256, ((3 * mean / 2 + 127) / 128) * 128));
   std::vector<int4> chunks;
   std::vector<int> slot0(c->ntiles, -1), nchunk(c->ntiles, 0);
   int nslots = 0;
@@ -289,9 +316,26 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   std::stable_sort(chunks.begin(), chunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
   c->nchunks = (int)chunks.size();
   c->nslots = nslots;
+  // degridding work units: each tile's home visibilities (a run of the sorted
+  // order) in chunks of at most dch; dch keeps the number of chunks (the grid
+  // of the kernel, whose FP64 partial sums use one slot per block) within
+  // kMaxPartials: at most ntiles + M / dch <= 16384 + 16384
+  const int64_t dch = std::max<int64_t>(1024, (2 * M + kMaxPartials - 1) / kMaxPartials);
+  std::vector<int4> dchunks;
+  for (int t = 0; t < c->ntiles; ++t) {
+    const int b = cnt[t], e = cnt[t + 1];
+    const int nc = (int)((e - b + dch - 1) / dch);
+    for (int k = 0; k < nc; ++k) {
+      const int cb = b + (int)((int64_t)(e - b) * k / nc), ce = b + (int)((int64_t)(e - b) * (k + 1) / nc);
+      dchunks.push_back(make_int4(t, cb, ce, 0));
+    }
+  }
+  std::stable_sort(dchunks.begin(), dchunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  c->ndchunks = (int)dchunks.size();
   if ((st = dev_alloc(&c->d_uv, M)) == PURIFY_OK && (st = dev_alloc(&c->d_perm, M)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_list, c->nlist)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_chunks, c->nchunks)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_dchunks, std::max(1, c->ndchunks))) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_slot0, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_nchunk, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_cnt, c->ntiles)) == PURIFY_OK &&
@@ -299,6 +343,8 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
     cudaMemcpyAsync(c->d_perm, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_list, list.data(), c->nlist * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_chunks, chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (c->ndchunks > 0)
+      cudaMemcpyAsync(c->d_dchunks, dchunks.data(), c->ndchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_slot0, slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_nchunk, nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->d_tile_cnt, 0, c->ntiles * sizeof(unsigned), s);

@@ -181,6 +181,9 @@ struct purify_ctx {
   unsigned* d_tile_cnt; // arrival counters (zero between launches)
   int nslots;
   float2* d_slots;      // nslots x tileT^2 partial tiles
+  // degridding work units: (tile, begin, end, -) runs of home visibilities
+  int ndchunks;
+  int4* d_dchunks;
 
   // scratch
   float2* d_grid;       // L x L

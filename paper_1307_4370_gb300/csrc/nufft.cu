@@ -123,15 +123,31 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
 }
 
 // ---------------------------------------------------------------------------
-// Degridding G: one thread per (sorted) visibility.
+// Degridding G.  The visibilities are sorted by the grid tile (T x T) holding
+// the first cell of their footprint; one CTA takes a run of one tile's
+// visibilities, stages the (T + J - 1)^2 cells their footprints can reach in
+// shared memory, and gathers J x J cells per visibility from there.
 // ---------------------------------------------------------------------------
 template <int J, int MODE>
-__global__ void k_degrid(const float2* __restrict__ X, const float2* __restrict__ uv,
-                         const int* __restrict__ perm, DegridArgs a, KbPoly kb, KappaScale ks,
-                         int L, int64_t M, double* partials, DevScalars* sc) {
+__global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, const float2* __restrict__ uv,
+                                                const int* __restrict__ perm, DegridArgs a,
+                                                const int4* __restrict__ dchunks, KbPoly kb, KappaScale ks, int L,
+                                                int T, int tiles_1d, double* partials, DevScalars* sc) {
+  extern __shared__ float2 halo[];
+  const int W = T + J - 1;
+  const int4 ch = dchunks[blockIdx.x];
+  const int tr = ch.x / tiles_1d, tc = ch.x - tr * tiles_1d;
+  const int R0 = tr * T, C0 = tc * T;
+  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+    const int rr = idx / W, cc = idx - rr * W;
+    int r = R0 + rr, c = C0 + cc;
+    if (r >= L) r -= L;
+    if (c >= L) c -= L;
+    halo[idx] = __ldg(&X[(size_t)r * L + c]);
+  }
+  __syncthreads();
   double acc2[2] = {0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
     const float2 u = __ldg(&uv[i]);
     int k0r, k0c;
     float fr, fc;
@@ -142,22 +158,37 @@ __global__ void k_degrid(const float2* __restrict__ X, const float2* __restrict_
     float wr[J], wc[J];
     kb_weights<J>(kb, fr, wr);
     kb_weights<J>(kb, fc, wc);
-    int col[J];
-#pragma unroll
-    for (int b = 0; b < J; ++b) col[b] = wrap(k0c + b, L);
+    const int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
     float2 acc = make_float2(0.f, 0.f);
+    if (dr < T && dc < T) {
+      const float2* base = halo + dr * W + dc;
 #pragma unroll
-    for (int aa = 0; aa < J; ++aa) {
-      const float2* row = X + (size_t)wrap(k0r + aa, L) * L;
-      float2 t = make_float2(0.f, 0.f);
+      for (int aa = 0; aa < J; ++aa) {
+        float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < J; ++b) {
-        const float2 g = __ldg(&row[col[b]]);
-        t.x = fmaf(wc[b], g.x, t.x);
-        t.y = fmaf(wc[b], g.y, t.y);
+        for (int b = 0; b < J; ++b) {
+          const float2 g = base[aa * W + b];
+          t.x = fmaf(wc[b], g.x, t.x);
+          t.y = fmaf(wc[b], g.y, t.y);
+        }
+        acc.x = fmaf(wr[aa], t.x, acc.x);
+        acc.y = fmaf(wr[aa], t.y, acc.y);
       }
-      acc.x = fmaf(wr[aa], t.x, acc.x);
-      acc.y = fmaf(wr[aa], t.y, acc.y);
+    } else {
+      // not in this tile (never for a consistent table): read the grid directly
+#pragma unroll
+      for (int aa = 0; aa < J; ++aa) {
+        const float2* row = X + (size_t)wrap(k0r + aa, L) * L;
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < J; ++b) {
+          const float2 g = __ldg(&row[wrap(k0c + b, L)]);
+          t.x = fmaf(wc[b], g.x, t.x);
+          t.y = fmaf(wc[b], g.y, t.y);
+        }
+        acc.x = fmaf(wr[aa], t.x, acc.x);
+        acc.y = fmaf(wr[aa], t.y, acc.y);
+      }
     }
     if (MODE == kDegridPerm) {
       a.out[perm[i]] = acc;
@@ -194,13 +225,16 @@ __global__ void k_degrid(const float2* __restrict__ X, const float2* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Gridding G^T.  The grid is cut into T x T tiles; set-up listed, per tile,
-// the visibilities whose footprint meets it and cut each list into chunks of
-// at most chunk_max entries.  One CTA per chunk sums the contributions that
-// fall inside its tile in shared memory.  A tile with one chunk is written to
-// X directly; otherwise each chunk stores a partial tile and the last chunk
-// to finish adds the partials in chunk order and writes the tile, so every
-// grid cell is written exactly once and no global atomics touch the data.
+// Gridding G^T, as a gather (no atomics).  The grid is cut into T x T tiles;
+// set-up listed, per tile, the visibilities whose footprint meets it, sorted
+// by the footprint's first cell relative to the tile (one run per start
+// cell), and cut each list into chunks.  One CTA per chunk stages its
+// entries (start cell, value, J + J kernel weights) in shared memory; each
+// thread owns a 2 x 2 block of cells and sums, in a fixed order, the entries
+// of the (J + 1)^2 start cells whose footprint reaches it.  A tile with one
+// chunk is written to X directly; otherwise each chunk stores a partial tile
+// and the last chunk to finish adds the partials in chunk order.  Every cell
+// is written once and the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
 template <int J, int MODE>
 __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
@@ -208,20 +242,23 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
                                               const int* __restrict__ tile_list, const int4* __restrict__ chunks,
                                               const int* __restrict__ tile_slot0, const int* __restrict__ tile_nchunk,
                                               unsigned* __restrict__ tile_cnt, float2* __restrict__ slots, KbPoly kb,
-                                              KappaScale ks, int L, int T, int tiles_1d) {
-  extern __shared__ float smf[];
+                                              KappaScale ks, int L, int T, int tiles_1d, int chunk_max) {
+  extern __shared__ float4 sm4[];
   __shared__ bool s_last;
-  float* accr = smf;
-  float* acci = smf + T * T;
+  const int W = T + J - 1;
+  const int NK = W * W;
+  float2* yv = reinterpret_cast<float2*>(sm4);                 // chunk_max values
+  float* wt = reinterpret_cast<float*>(yv + chunk_max);        // chunk_max x 2J weights
+  int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * 2 * J);  // chunk_max keys
+  int* off = key + chunk_max;                                  // NK + 1 run offsets
   const int4 ch = chunks[blockIdx.x];
   const int tile = ch.x;
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
-  const int TT = T * T;
-  for (int k = threadIdx.x; k < TT; k += blockDim.x) { accr[k] = 0.f; acci[k] = 0.f; }
-  __syncthreads();
-  for (int e = ch.y + threadIdx.x; e < ch.z; e += blockDim.x) {
-    const int i = tile_list[e];
+  const int ne = ch.z - ch.y;
+  // stage the chunk's entries
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int i = tile_list[ch.y + e];
     const float2 u = __ldg(&uv[i]);
     const float2 val = (MODE == kGridPerm) ? __ldg(&vis[perm[i]]) : __ldg(&vis[i]);
     int k0r, k0c;
@@ -233,34 +270,68 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
     float wr[J], wc[J];
     kb_weights<J>(kb, fr, wr);
     kb_weights<J>(kb, fc, wc);
-    // offsets of the footprint relative to the tile origin (wrapped)
-    const int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
+    int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
+    if (dr >= L - (J - 1)) dr -= L;
+    if (dc >= L - (J - 1)) dc -= L;
+    const bool inside = dr < T && dc < T;  // always, for a consistent table
+    key[e] = inside ? (dr + J - 1) * W + (dc + J - 1) : NK;
+    yv[e] = val;
 #pragma unroll
-    for (int aa = 0; aa < J; ++aa) {
-      int rr = dr + aa;
-      if (rr >= L) rr -= L;
-      if (rr >= T) continue;
-      const float2 vr = make_float2(wr[aa] * val.x, wr[aa] * val.y);
-#pragma unroll
-      for (int b = 0; b < J; ++b) {
-        int cc = dc + b;
-        if (cc >= L) cc -= L;
-        if (cc >= T) continue;
-        atomicAdd(&accr[rr * T + cc], wc[b] * vr.x);
-        atomicAdd(&acci[rr * T + cc], wc[b] * vr.y);
-      }
+    for (int k = 0; k < J; ++k) {
+      wt[e * 2 * J + k] = wr[k];
+      wt[e * 2 * J + J + k] = wc[k];
     }
   }
   __syncthreads();
-  if (ch.w < 0) {
-    for (int k = threadIdx.x; k < TT; k += blockDim.x) {
-      const int rr = k / T, cc = k - rr * T;
-      X[(size_t)(R0 + rr) * L + C0 + cc] = make_float2(accr[k], acci[k]);
+  // off[k] = first entry with key >= k (entries are sorted by key)
+  for (int k = threadIdx.x; k <= NK; k += blockDim.x) {
+    int lo = 0, hi = ne;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key[mid] < k) lo = mid + 1;
+      else hi = mid;
     }
-    return;
+    off[k] = lo;
   }
-  float2* mine = slots + (size_t)ch.w * TT;
-  for (int k = threadIdx.x; k < TT; k += blockDim.x) mine[k] = make_float2(accr[k], acci[k]);
+  __syncthreads();
+  const int HB = T / 2;
+  const bool multi = ch.w >= 0;
+  float2* dst = multi ? slots + (size_t)ch.w * T * T : nullptr;
+  for (int blk = threadIdx.x; blk < HB * HB; blk += blockDim.x) {
+    const int R = 2 * (blk / HB), C = 2 * (blk - (blk / HB) * HB);
+    float2 acc00 = make_float2(0.f, 0.f), acc01 = acc00, acc10 = acc00, acc11 = acc00;
+    // start rows sr in [R - J + 1, R + 1], i.e. key rows R .. R + J
+    for (int kr = R; kr <= R + J; ++kr) {
+      const int a0 = R + J - 1 - kr;  // row tap of cell row R (valid if 0 <= a0 < J)
+      const int kbase = kr * W;
+      const int e0 = off[kbase + C], e1 = off[kbase + C + J + 1];  // key cols C .. C + J
+      for (int e = e0; e < e1; ++e) {
+        const int kc = key[e] - kbase;
+        const int b0 = C + J - 1 - kc;  // column tap of cell column C
+        const float2 v = yv[e];
+        const float* w = wt + e * 2 * J;
+        const float wc0 = (b0 >= 0 && b0 < J) ? w[J + b0] : 0.f;
+        const float wc1 = (b0 + 1 >= 0 && b0 + 1 < J) ? w[J + b0 + 1] : 0.f;
+        const float wr0 = (a0 >= 0 && a0 < J) ? w[a0] : 0.f;
+        const float wr1 = (a0 + 1 >= 0 && a0 + 1 < J) ? w[a0 + 1] : 0.f;
+        const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
+        acc00.x = fmaf(wc0, v0.x, acc00.x); acc00.y = fmaf(wc0, v0.y, acc00.y);
+        acc01.x = fmaf(wc1, v0.x, acc01.x); acc01.y = fmaf(wc1, v0.y, acc01.y);
+        acc10.x = fmaf(wc0, v1.x, acc10.x); acc10.y = fmaf(wc0, v1.y, acc10.y);
+        acc11.x = fmaf(wc1, v1.x, acc11.x); acc11.y = fmaf(wc1, v1.y, acc11.y);
+      }
+    }
+    if (!multi) {
+      float2* row0 = X + (size_t)(R0 + R) * L + C0 + C;
+      float2* row1 = row0 + L;
+      reinterpret_cast<float4*>(row0)[0] = make_float4(acc00.x, acc00.y, acc01.x, acc01.y);
+      reinterpret_cast<float4*>(row1)[0] = make_float4(acc10.x, acc10.y, acc11.x, acc11.y);
+    } else {
+      reinterpret_cast<float4*>(dst + R * T + C)[0] = make_float4(acc00.x, acc00.y, acc01.x, acc01.y);
+      reinterpret_cast<float4*>(dst + (R + 1) * T + C)[0] = make_float4(acc10.x, acc10.y, acc11.x, acc11.y);
+    }
+  }
+  if (!multi) return;
   __threadfence();
   __syncthreads();
   const int nc = tile_nchunk[tile];
@@ -268,6 +339,7 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  const int TT = T * T;
   const float2* first = slots + (size_t)tile_slot0[tile] * TT;
   for (int k = threadIdx.x; k < TT; k += blockDim.x) {
     float2 sum = make_float2(0.f, 0.f);
@@ -403,12 +475,16 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
 template <int J>
 static void degrid_J(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
   const int threads = 256;
-  int64_t blocks = (c->M + threads - 1) / threads;
-  if (blocks > kMaxPartials) blocks = kMaxPartials;
-#define DEG(MD)                                                                                              \
-  PURIFY_LAUNCH(c, "degrid", s,                                                                              \
-                (k_degrid<J, MD><<<(unsigned)blocks, threads, 0, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->kb, \
-                                                                      c->ks, c->L, c->M, c->d_partials, c->d_sc)))
+  const int W = c->tileT + J - 1;
+  const size_t sm = (size_t)W * W * sizeof(float2);
+#define DEG(MD)                                                                                               \
+  do {                                                                                                        \
+    allow_smem(k_degrid<J, MD>, sm);                                                                          \
+    PURIFY_LAUNCH(c, "degrid", s,                                                                             \
+                  (k_degrid<J, MD><<<c->ndchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->d_dchunks, \
+                                                                    c->kb, c->ks, c->L, c->tileT, c->tiles_1d,     \
+                                                                    c->d_partials, c->d_sc)));                     \
+  } while (0)
   if (mode == kDegridPerm) DEG(kDegridPerm);
   else if (mode == kDegridSorted) DEG(kDegridSorted);
   else DEG(kDegridSdmm);
@@ -426,15 +502,25 @@ int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
 }
 
 template <int J>
+static size_t grid_smem(const purify_ctx* c) {
+  const int W = c->tileT + J - 1;
+  return (size_t)c->chunk_max * (8 + 8 * J + 4) + (size_t)(W * W + 1) * 4;
+}
+
+template <int J>
 static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
-  const int threads = 256;
-  const size_t sm = 2 * (size_t)c->tileT * c->tileT * sizeof(float);
-#define GRD(MD)                                                                                             \
-  PURIFY_LAUNCH(c, "grid", s,                                                                               \
-                (k_grid<J, MD><<<c->nchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_list, \
-                                                               c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
-                                                               c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L,       \
-                                                               c->tileT, c->tiles_1d)))
+  const int HB = c->tileT / 2;
+  const int threads = HB * HB < 64 ? 64 : (HB * HB > 256 ? 256 : HB * HB);
+  const size_t sm = grid_smem<J>(c);
+#define GRD(MD)                                                                                                \
+  do {                                                                                                         \
+    allow_smem(k_grid<J, MD>, sm);                                                                             \
+    PURIFY_LAUNCH(c, "grid", s,                                                                                \
+                  (k_grid<J, MD><<<c->nchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_list, \
+                                                                 c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
+                                                                 c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L,       \
+                                                                 c->tileT, c->tiles_1d, c->chunk_max)));             \
+  } while (0)
   if (mode == kGridPerm) GRD(kGridPerm);
   else GRD(kGridSorted);
 #undef GRD
