@@ -123,6 +123,27 @@ int purify_sizes(const purify_ctx* ctx, int64_t* N, int64_t* M, int32_t* q,
  * purify_create. */
 int purify_phi(purify_ctx* ctx, const float* x, float* y, purify_stream_t stream);
 
+/* y = Phi x without allocating anything and without a context.  The paper
+ * has no counterpart: this is for callers that cannot allocate device memory
+ * at the point where they need Phi -- a process whose GPU memory is already
+ * reserved in full by another allocator, or a latency-critical loop that
+ * cannot afford cudaMalloc and the device synchronisation it implies
+ * (purify_create allocates its tables and scratch).  Same arithmetic as
+ * purify_phi, visibilities gathered in the given order.
+ *   n   image side, 8 <= n <= 256, even, 2n = 2^a 3^b with b <= 1
+ *   J   Kaiser-Bessel support: 2, 4, 6 or 8;  M >= 1 visibilities
+ *   uv  M float32 pairs, x N = n*n complex64, y M complex64 (all device,
+ *       owned by the caller).
+ * Scratch: one fixed array (about 3 MiB) in the library's device memory,
+ * held by every GPU that loads the library until the process exits.  All
+ * calls share it and it keeps the last call's contents: calls that overlap on
+ * the GPU race; order them on one stream.  The first call on a device looks
+ * up the array's device address with that device current, so make it before
+ * any stream capture.  Sizes beyond the limits return PURIFY_E_SIZE (or
+ * PURIFY_E_UNSUPPORTED for the grid side). */
+int purify_phi_static(int32_t n, int32_t J, int64_t M, const float* uv, const float* x,
+                      float* y, purify_stream_t stream);
+
 /* x = Phi^H y = Z^T D F^H G^T y: y is M complex64, x is N complex64. */
 int purify_phi_adj(purify_ctx* ctx, const float* y, float* x, purify_stream_t stream);
 

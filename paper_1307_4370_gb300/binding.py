@@ -64,6 +64,7 @@ _SIGS = {
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "purify_phi_static": (ctypes.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _vp]),
     "purify_phi_adj": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "purify_sara_analysis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "purify_sara_synthesis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -309,6 +310,20 @@ class Context:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().purify_launch_count())
+
+
+def phi_static(n: int, J: int, uv: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """y = Phi x through purify_phi_static (no context, no allocation in the library)."""
+    lib = load()
+    M = int(uv.shape[0])
+    if uv.dtype != torch.float32 or not uv.is_cuda or uv.dim() != 2 or uv.shape[1] != 2:
+        raise ValueError("uv: (M, 2) float32 on a CUDA device")
+    x = _c64(x, n * n, "x")
+    y = out if out is not None else torch.empty(M, dtype=torch.complex64, device=x.device)
+    _check("purify_phi_static", lib.purify_phi_static(int(n), int(J), M, _ptr(uv.contiguous()), _ptr(x), _ptr(y),
+                                                      _stream(stream)))
+    return y
 
 
 def default_params() -> SdmmParams:
