@@ -170,14 +170,15 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
     c = 8
     D = q * N
     return {
-        # read x (or r, p; write p in CG steps), write n x 2n rows
-        "row_fwd": (k * (5 * N * c) + 3 * N * c) / (k + 1),
+        # first CG step: read r; later steps and the x_hat pass: read r, w, p, s, x,
+        # write p, s, x, r (single-reduction CG update); always write n x 2n rows
+        "row_fwd": ((3 + (k - 1) * 11 + 11) * N * c) / (k + 1),
         "col_fwd": 6 * N * c,                          # read n x 2n, write 2n x 2n
         "degrid": (k * (4 * N * c + 2 * M * c) + (4 * N * c + 4 * M * c)) / (k + 1),
         "grid": 4 * N * c + 2 * M * c,                 # read uv + vis, write the grid
         "col_inv": 6 * N * c,
-        "row_inv": (k * (5 * N * c) + 9 * N * c) / (k + 1),
-        "cg_update": 6 * N * c,
+        # CG: read n x 2n rows and r, write w; SDMM: also x_hat, z3, x1 in, z3 out
+        "row_inv": (k * 4 * N * c + 7 * N * c) / (k + 1),
         "sdmm_l2": 5 * M * c,                          # s2, z2, y in; z2, v out
         # all levels of all planes: x in, z1 / w in, z1 / u1 out (w float32)
         "dwt_level": (N * c + D * (c + 4 + 2 * c)) / 4,

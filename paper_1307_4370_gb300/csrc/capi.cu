@@ -356,18 +356,27 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   return st;
 }
 
-// One CG step on Q = Phi^H Phi + 2I (state in x, r, p; Qp into qp).
-int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* qp, cudaStream_t s) {
-  TRY(phi_forward_grid(c, kRowInCgDir, RowInArgs{r, p}, s));
+// One step of single-reduction CG on Q = Phi^H Phi + 2I: apply the pending
+// update of the previous step (not before the first step), w = Q r, and the
+// step sizes from <r, r> and <w, r> (Chronopoulos & Gear 1989; in exact
+// arithmetic the iterates are those of the standard CG of the x-update).
+int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, float2* w, bool first, cudaStream_t s) {
+  RowInArgs ia{};
+  ia.in = r;
+  ia.x = x;
+  ia.r = r;
+  ia.p = p;
+  ia.s = sv;
+  ia.w = w;
+  TRY(phi_forward_grid(c, first ? kRowInPlain : kRowInCgUpd, ia, s));
   DegridArgs da{};
   da.out = c->d_vis;
   TRY(degrid(c, kDegridSorted, da, s));
   TRY(grid_adjoint(c, kGridSorted, c->d_vis, s));
   RowOutArgs ra{};
-  ra.out = qp;
-  ra.p = p;
-  TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s));
-  return launch_cg_update(c, x, r, p, qp, s);
+  ra.out = w;
+  ra.p = r;
+  return phi_adjoint_image(c, kRowOutCgQ, ra, s);
 }
 
 int64_t ctx_N(const purify_ctx* c) { return (int64_t)c->n * c->n; }
@@ -385,10 +394,18 @@ int load_data(purify_ctx* c, purify_sdmm_state* st, const float* y, cudaStream_t
 // Algorithm 1 steps 5-9 for one iteration, enqueued on s.
 int enqueue_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
-  // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r, p hold r0 = b - Q x_hat(t-1))
-  for (int k = 0; k < st->params.cg_iters; ++k) TRY(cg_step(c, st->xhat, st->r, st->p, st->qp, s));
-  // i = 2, first half: s2 = Phi x_hat and the l2 norms (FP64)
-  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{st->xhat, nullptr}, s));
+  // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r holds r0 = b - Q x_hat(t-1))
+  const int k = st->params.cg_iters;
+  for (int i = 0; i < k; ++i) TRY(cg_step(c, st->xhat, st->r, st->p, st->sv, st->qp, i == 0, s));
+  // i = 2, first half: s2 = Phi x_hat (after the last CG update) and the l2 norms (FP64)
+  RowInArgs ia{};
+  ia.in = st->xhat;
+  ia.x = st->xhat;
+  ia.r = st->r;
+  ia.p = st->p;
+  ia.s = st->sv;
+  ia.w = st->qp;
+  TRY(phi_forward_grid(c, k > 0 ? kRowInCgFinish : kRowInPlain, ia, s));
   DegridArgs da{};
   da.out = st->s2;
   da.z2 = st->z2;
@@ -410,7 +427,6 @@ int enqueue_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   ra.p = st->xhat;
   ra.x1 = st->x1;
   ra.z3 = st->z3;
-  ra.pdir = st->p;
   TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s));
   st->launches_per_step = (int)(g_launches.load(std::memory_order_relaxed) - l0);
   return PURIFY_OK;
@@ -539,7 +555,9 @@ int purify_phi(purify_ctx* c, const float* x, float* y, purify_stream_t stream) 
   DeviceGuard g(c->device);
   if (!is_device_ptr(x) || !is_device_ptr(y)) return PURIFY_E_NOT_DEVICE_PTR;
   cudaStream_t s = (cudaStream_t)stream;
-  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{(const float2*)x, nullptr}, s));
+  RowInArgs ia{};
+  ia.in = (const float2*)x;
+  TRY(phi_forward_grid(c, kRowInPlain, ia, s));
   DegridArgs da{};
   da.out = (float2*)y;
   return degrid(c, kDegridPerm, da, s);
@@ -613,19 +631,22 @@ int purify_cg_solve(purify_ctx* c, const float* b, float* x, int32_t iters, doub
     return PURIFY_E_NOT_DEVICE_PTR;
   cudaStream_t s = (cudaStream_t)stream;
   float2* X = (float2*)x;
-  float2 *r = c->d_img[0], *p = c->d_img[1], *qp = c->d_img[2];
-  // Q x0 through the CG epilogue (p := x0), then r = b - Q x0, p = r
-  TRY(phi_forward_grid(c, kRowInPlain, RowInArgs{X, nullptr}, s));
+  float2 *r = c->d_img[0], *p = c->d_img[1], *sv = c->d_img[2], *w = c->d_img[3];
+  // Q x0 (into w), then r = b - Q x0
+  RowInArgs ia{};
+  ia.in = X;
+  TRY(phi_forward_grid(c, kRowInPlain, ia, s));
   DegridArgs da{};
   da.out = c->d_vis;
   TRY(degrid(c, kDegridSorted, da, s));
   TRY(grid_adjoint(c, kGridSorted, c->d_vis, s));
   RowOutArgs ra{};
-  ra.out = qp;
+  ra.out = w;
   ra.p = X;
   TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s));
-  TRY(launch_cg_residual_init(c, (const float2*)b, qp, r, p, s));
-  for (int k = 0; k < iters; ++k) TRY(cg_step(c, X, r, p, qp, s));
+  TRY(launch_cg_residual_init(c, (const float2*)b, w, r, s));
+  for (int k = 0; k < iters; ++k) TRY(cg_step(c, X, r, p, sv, w, k == 0, s));
+  if (iters > 0) TRY(launch_cg_apply(c, X, r, p, sv, w, s));
   if (resid_out) TRY_CUDA(cudaMemcpyAsync(resid_out, &c->d_sc->cg_res, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return PURIFY_OK;
 }
@@ -651,7 +672,7 @@ void purify_sdmm_state_destroy(purify_sdmm_state* st) {
   cudaDeviceSynchronize();
   drop_graph(st);
   if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
-  void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->x1, st->z3, st->z1, st->u1,
+  void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->sv, st->x1, st->z3, st->z1, st->u1,
                   st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -668,7 +689,8 @@ int purify_sdmm_state_create(purify_ctx* c, purify_sdmm_state** out) {
   const int64_t N = ctx_N(c), D = ctx_D(c), M = c->M;
   int e;
   if ((e = dev_alloc(&st->xhat, N)) || (e = dev_alloc(&st->r, N)) || (e = dev_alloc(&st->p, N)) ||
-      (e = dev_alloc(&st->qp, N)) || (e = dev_alloc(&st->x1, N)) || (e = dev_alloc(&st->z3, N)) ||
+      (e = dev_alloc(&st->qp, N)) || (e = dev_alloc(&st->sv, N)) || (e = dev_alloc(&st->x1, N)) ||
+      (e = dev_alloc(&st->z3, N)) ||
       (e = dev_alloc(&st->z1, D)) || (e = dev_alloc(&st->u1, D)) || (e = dev_alloc(&st->w, D)) ||
       (e = dev_alloc(&st->y, M)) || (e = dev_alloc(&st->yb, 2 * M)) || (e = dev_alloc(&st->yscale, (M + 4095) / 4096)) ||
       (e = dev_alloc(&st->z2, M)) || (e = dev_alloc(&st->s2, M)) || (e = dev_alloc(&st->v, M))) {
@@ -711,6 +733,7 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   TRY_CUDA(cudaMemsetAsync(st->r, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->p, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->qp, 0, N * sizeof(float2), s));
+  TRY_CUDA(cudaMemsetAsync(st->sv, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->x1, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->z3, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->z1, 0, D * sizeof(float2), s));
@@ -723,6 +746,7 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   // scalars: everything zero but eps
   DevScalars z{};
   z.eps = eps;
+  z.cg_first = 1;
   std::memcpy(c->h_sc, &z, sizeof(z));
   TRY_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
   // gamma = beta ||Psi^H Phi^H y||_inf (§4.4), via Phi^H y (sorted) into x1 and Psi^H into u1

@@ -124,6 +124,8 @@ struct DevScalars {
   double zeta, nu;   // halting quantities
   double iters;
   double cg_res;
+  int cg_first;      // the next Q-epilogue starts a CG solve
+  int upd_first;     // the pending CG update is the first of a solve (p = r, s = w)
   unsigned int counter[kNumCounters];
 };
 
@@ -238,7 +240,8 @@ struct purify_sdmm_state {
   float2* xhat;   // N
   float2* r;      // N  CG residual
   float2* p;      // N  CG direction
-  float2* qp;     // N  Q p
+  float2* qp;     // N  w = Q r
+  float2* sv;     // N  s = Q p (single-reduction CG)
   float2* x1;     // N  Psi u1
   float2* z3;     // N
   // coefficient-size vectors
@@ -269,14 +272,22 @@ namespace purify {
 int check_cuda(cudaError_t e);
 
 // nufft.cu
-enum RowInMode { kRowInPlain = 0, kRowInCgDir = 1 };
+// kRowInCgUpd: apply the pending CG vector update, then transform r;
+// kRowInCgFinish: apply it, then transform x.
+enum RowInMode { kRowInPlain = 0, kRowInCgUpd = 1, kRowInCgFinish = 2 };
 enum DegridOut { kDegridPerm = 0, kDegridSorted = 1, kDegridSdmm = 2 };
 enum GridIn { kGridPerm = 0, kGridSorted = 1 };
 enum RowOutMode { kRowOutPlain = 0, kRowOutCgQ = 1, kRowOutSdmm = 2 };
 
 struct RowInArgs {
-  const float2* x;      // image (plain) or r (cg)
-  float2* p;            // cg: direction, updated in place to r + beta p
+  const float2* in;     // plain: the image to transform
+  // CG (single-reduction form): the pending update of step i-1 is
+  //   p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
+  float2* x;
+  float2* r;
+  float2* p;
+  float2* s;
+  const float2* w;
 };
 struct DegridArgs {
   float2* out;              // y (perm) or sorted output
@@ -286,11 +297,10 @@ struct DegridArgs {
   const float* yscale;
 };
 struct RowOutArgs {
-  float2* out;          // plain: image; cg: Qp; sdmm: r0
-  const float2* p;      // cg: p; sdmm: x_hat
+  float2* out;          // plain: image; cg: w = Q r; sdmm: r0
+  const float2* p;      // cg: r (the vector Q is applied to); sdmm: x_hat
   const float2* x1;     // sdmm: Psi u1
   float2* z3;           // sdmm
-  float2* pdir;         // sdmm: p0 = r0
 };
 
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s);
@@ -317,10 +327,8 @@ int launch_l2_norm_diff(purify_ctx* c, int64_t count, const float2* a, const flo
 int launch_l2_project(int64_t count, const float2* in, const float2* y, double eps,
                       const double* norm2_dev, float2* out, cudaStream_t s);
 int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s);
-int launch_cg_update(purify_ctx* c, float2* x, float2* r, const float2* p, const float2* qp,
-                     cudaStream_t s);
-int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, float2* p,
-                            cudaStream_t s);
+int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, cudaStream_t s);
+int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, cudaStream_t s);
 int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s);
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s);
 int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round,

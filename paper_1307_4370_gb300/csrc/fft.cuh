@@ -82,7 +82,7 @@ struct SigLayout {
 // element-fastest.  nsig * L == blockDim.x * EPT.
 template <int R, int EPT, bool SIG_FAST>
 __device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L, int Ns, int nsig,
-                                               const float2* __restrict__ tw) {
+                                               const float2* tw) {
   static_assert(EPT % R == 0, "radix must divide elements per thread");
   constexpr int NB = EPT / R;
   const int nthr = blockDim.x;
@@ -100,7 +100,7 @@ __device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L
     for (int r = 0; r < R; ++r) v[k * R + r] = buf[lay.at(s, j + r * LR)];
     if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], __ldg(&tw[r * kk * twstep]));
+      for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], tw[r * kk * twstep]);
     }
     dft_small<R>(&v[k * R]);
   }

@@ -57,8 +57,11 @@ static void allow_smem(K kernel, size_t bytes) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward row pass: g[r][e] = x[r][c] / (ghat_r ghat_c) / L at e = (c - n/2) mod L,
-// then the row DFT; rows stored in `half` (n x L).
+// Forward row pass: g[r][e] = v[r][c] / (ghat_r ghat_c) / L at e = (c - n/2) mod L,
+// then the row DFT; rows stored in `half` (n x L).  In the CG modes the pixel
+// first receives the pending vector update of the previous CG step
+// (single-reduction CG: p = r + beta p, s = w + beta s, x += alpha p,
+// r -= alpha s), and v is the new r (kRowInCgUpd) or x (kRowInCgFinish).
 // ---------------------------------------------------------------------------
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
@@ -66,10 +69,17 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
                           const DevScalars* __restrict__ sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int r0 = blockIdx.x * nsig;
   const float invL = 1.0f / (float)L;
-  float beta = 0.0f;
-  if (MODE == kRowInCgDir) beta = (float)sc->beta;
+  float alpha = 0.f, beta = 0.f;
+  bool first = false;
+  if (MODE != kRowInPlain) {
+    alpha = (float)sc->alpha;
+    beta = (float)sc->beta;
+    first = sc->upd_first != 0;
+  }
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int s = idx / L, e = idx - s * L;
     const int r = r0 + s;
@@ -78,12 +88,27 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
     float2 v = make_float2(0.f, 0.f);
     if (cc < n) {
       const size_t off = (size_t)r * n + cc;
-      if (MODE == kRowInCgDir) {
-        float2 rr = a.x[off], pp = a.p[off];
-        v = make_float2(fmaf(beta, pp.x, rr.x), fmaf(beta, pp.y, rr.y));
-        a.p[off] = v;
+      if (MODE == kRowInPlain) {
+        v = a.in[off];
       } else {
-        v = a.x[off];
+        const float2 rr = a.r[off], ww = a.w[off];
+        float2 pp, ss;
+        if (first) {
+          pp = rr;
+          ss = ww;
+        } else {
+          const float2 po = a.p[off], so = a.s[off];
+          pp = make_float2(fmaf(beta, po.x, rr.x), fmaf(beta, po.y, rr.y));
+          ss = make_float2(fmaf(beta, so.x, ww.x), fmaf(beta, so.y, ww.y));
+        }
+        float2 xx = a.x[off];
+        xx = make_float2(fmaf(alpha, pp.x, xx.x), fmaf(alpha, pp.y, xx.y));
+        const float2 rn = make_float2(fmaf(-alpha, ss.x, rr.x), fmaf(-alpha, ss.y, rr.y));
+        a.p[off] = pp;
+        a.s[off] = ss;
+        a.x[off] = xx;
+        a.r[off] = rn;
+        v = (MODE == kRowInCgUpd) ? rn : xx;
       }
       const float f = dz[r] * dz[cc] * invL;
       v = cscale(v, f);
@@ -91,7 +116,7 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
     sm[s * L + e] = v;
   }
   __syncthreads();
-  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tw);
+  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int s = idx / L, e = idx - s * L;
     half[(size_t)(r0 + s) * L + e] = sm[s * L + e];
@@ -107,6 +132,8 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
                           const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int c0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int e = idx / nsig, s = idx - e * nsig;
@@ -115,7 +142,7 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
     sm[e * nsig + s] = (r < n) ? half[(size_t)r * L + c0 + s] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tw);
+  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int e = idx / nsig, s = idx - e * nsig;
     X[(size_t)e * L + c0 + s] = sm[e * nsig + s];
@@ -358,13 +385,15 @@ __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, 
                           const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int c0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int e = idx / nsig, s = idx - e * nsig;
     sm[e * nsig + s] = cconj(X[(size_t)e * L + c0 + s]);
   }
   __syncthreads();
-  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tw);
+  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
     const int r = idx / nsig, s = idx - r * nsig;
     int e = r - (n >> 1);
@@ -376,9 +405,12 @@ __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, 
 // ---------------------------------------------------------------------------
 // Inverse row pass, crop and deapodise, with epilogues:
 //   plain: out = Phi^H (.)
-//   CG:    out = Qp = Phi^H Phi p + 2p, and <p, Qp> (FP64) -> alpha = rho / <p,Qp>
+//   CG:    w = Q r = Phi^H Phi r + 2r with gamma = <r, r> and delta = <w, r>
+//          (FP64, one reduction); the last block forms the step sizes of
+//          single-reduction CG (Chronopoulos & Gear 1989):
+//          beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
 //   SDMM:  positivity branch (z3, u3) and the warm-start CG residual
-//          r0 = x1 + u3 - 2 x_hat + Phi^H v; p = r0; rho = ||r0||^2
+//          r0 = x1 + u3 - 2 x_hat + Phi^H v
 // ---------------------------------------------------------------------------
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ half, RowOutArgs a, const float* __restrict__ dz,
@@ -386,15 +418,17 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
                           double* partials, DevScalars* sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int r0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
     const int s = idx / L, e = idx - s * L;
     sm[s * L + e] = cconj(half[(size_t)(r0 + s) * L + e]);
   }
   __syncthreads();
-  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tw);
+  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
   const float invL = 1.0f / (float)L;
-  double acc = 0.0;
+  double acc[2] = {0.0, 0.0};
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
     const int s = idx / n, c = idx - s * n;
     const int r = r0 + s;
@@ -409,7 +443,8 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
       const float2 p = a.p[off];
       const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
       a.out[off] = q;
-      acc += (double)p.x * (double)q.x + (double)p.y * (double)q.y;  // Re <p, Qp>
+      acc[0] += (double)p.x * (double)p.x + (double)p.y * (double)p.y;  // <r, r>
+      acc[1] += (double)p.x * (double)q.x + (double)p.y * (double)q.y;  // Re <w, r>
     } else {
       const float2 xh = a.p[off];
       const float2 z3 = a.z3[off];
@@ -423,22 +458,25 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
       r0v.y = x1.y + u3.y - 2.f * xh.y + v.y;
       a.z3[off] = z3n;
       a.out[off] = r0v;
-      a.pdir[off] = r0v;
-      acc += (double)r0v.x * (double)r0v.x + (double)r0v.y * (double)r0v.y;
     }
   }
   if (MODE == kRowOutCgQ) {
-    double tot;
-    if (reduce_last_block<1>(&acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], &tot)) {
-      sc->pqp = tot;
-      sc->alpha = (tot > 0.0) ? sc->rho / tot : 0.0;
+    double tot[2];
+    if (reduce_last_block<2>(acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], tot)) {
+      const double gamma = tot[0], delta = tot[1];
+      const bool first = sc->cg_first != 0 || sc->alpha == 0.0 || sc->rho == 0.0;
+      const double beta = first ? 0.0 : gamma / sc->rho;
+      const double den = first ? delta : delta - beta * gamma / sc->alpha;
+      sc->pqp = den;
+      sc->beta = beta;
+      sc->alpha = den > 0.0 ? gamma / den : 0.0;
+      sc->rho = gamma;
+      sc->cg_res = sqrt(gamma);
+      sc->upd_first = first ? 1 : 0;
+      sc->cg_first = 0;
     }
   } else if (MODE == kRowOutSdmm) {
-    double tot;
-    if (reduce_last_block<1>(&acc, partials + kCntRho0 * 2 * kMaxPartials, &sc->counter[kCntRho0], &tot)) {
-      sc->rho = tot;
-      sc->beta = 0.0;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_first = 1;
   }
 }
 
@@ -447,17 +485,24 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
 // ---------------------------------------------------------------------------
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s) {
   const FftShape rs = row_shape(c), cs = col_shape(c);
-  const size_t smr = (size_t)rs.nsig * c->L * sizeof(float2);
-  const size_t smc = (size_t)cs.nsig * c->L * sizeof(float2);
+  const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
+  const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);
   const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
 #define ROWF(E, MD)                                                                                        \
-  PURIFY_LAUNCH(c, "row_fwd", s,                                                                           \
-                (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan, c->n, \
-                                                              rs.nsig, c->d_sc)))
+  do {                                                                                                     \
+    allow_smem(k_row_fwd<E, MD>, smr);                                                                     \
+    PURIFY_LAUNCH(c, "row_fwd", s,                                                                         \
+                  (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan,  \
+                                                                c->n, rs.nsig, c->d_sc)));                   \
+  } while (0)
   if (rs.ept == 8) {
-    if (mode == kRowInPlain) ROWF(8, kRowInPlain); else ROWF(8, kRowInCgDir);
+    if (mode == kRowInPlain) ROWF(8, kRowInPlain);
+    else if (mode == kRowInCgUpd) ROWF(8, kRowInCgUpd);
+    else ROWF(8, kRowInCgFinish);
   } else {
-    if (mode == kRowInPlain) ROWF(12, kRowInPlain); else ROWF(12, kRowInCgDir);
+    if (mode == kRowInPlain) ROWF(12, kRowInPlain);
+    else if (mode == kRowInCgUpd) ROWF(12, kRowInCgUpd);
+    else ROWF(12, kRowInCgFinish);
   }
 #undef ROWF
   if (cs.ept == 8) {
@@ -538,8 +583,8 @@ int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) 
 
 int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s) {
   const FftShape rs = row_shape(c), cs = col_shape(c);
-  const size_t smr = (size_t)rs.nsig * c->L * sizeof(float2);
-  const size_t smc = (size_t)cs.nsig * c->L * sizeof(float2);
+  const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
+  const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);
   const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
   if (cs.ept == 8) {
     allow_smem(k_col_inv<8>, smc);
@@ -551,9 +596,12 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
                   (k_col_inv<12><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
   }
 #define ROWI(E, MD)                                                                                          \
-  PURIFY_LAUNCH(c, "row_inv", s,                                                                             \
-                (k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan, c->n, \
-                                                              rs.nsig, c->d_partials, c->d_sc)))
+  do {                                                                                                       \
+    allow_smem(k_row_inv<E, MD>, smr);                                                                       \
+    PURIFY_LAUNCH(c, "row_inv", s,                                                                           \
+                  (k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan,  \
+                                                                c->n, rs.nsig, c->d_partials, c->d_sc)));     \
+  } while (0)
   if (rs.ept == 8) {
     if (mode == kRowOutPlain) ROWI(8, kRowOutPlain);
     else if (mode == kRowOutCgQ) ROWI(8, kRowOutCgQ);

@@ -63,47 +63,41 @@ __global__ void k_positive(int64_t n, const float2* __restrict__ in, float2* __r
   GRID_STRIDE(j, n) out[j] = make_float2(fmaxf(in[j].x, 0.f), 0.f);
 }
 
-// CG: x += alpha p; r -= alpha Qp; rho' = ||r||^2; beta = rho'/rho.
-__global__ void k_cg_update(int64_t n, float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
-                            const float2* __restrict__ qp, double* partials, DevScalars* sc) {
-  const float al = (float)sc->alpha;
+// The last pending update of a single-reduction CG solve (the earlier ones are
+// applied by the forward row pass of the next step):
+// p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s.
+__global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__ p,
+                           float2* __restrict__ sv, const float2* __restrict__ w, double* partials, DevScalars* sc) {
+  const float al = (float)sc->alpha, be = (float)sc->beta;
+  const bool first = sc->upd_first != 0;
   double acc = 0.0;
   GRID_STRIDE(j, n) {
-    const float2 pj = p[j], qj = qp[j];
-    float2 xj = x[j], rj = r[j];
-    xj.x = fmaf(al, pj.x, xj.x);
-    xj.y = fmaf(al, pj.y, xj.y);
-    rj.x = fmaf(-al, qj.x, rj.x);
-    rj.y = fmaf(-al, qj.y, rj.y);
-    x[j] = xj;
-    r[j] = rj;
-    acc += (double)rj.x * rj.x + (double)rj.y * rj.y;
+    const float2 rr = r[j], ww = w[j];
+    float2 pp, ss;
+    if (first) {
+      pp = rr;
+      ss = ww;
+    } else {
+      pp = make_float2(fmaf(be, p[j].x, rr.x), fmaf(be, p[j].y, rr.y));
+      ss = make_float2(fmaf(be, sv[j].x, ww.x), fmaf(be, sv[j].y, ww.y));
+    }
+    p[j] = pp;
+    sv[j] = ss;
+    x[j] = make_float2(fmaf(al, pp.x, x[j].x), fmaf(al, pp.y, x[j].y));
+    const float2 rn = make_float2(fmaf(-al, ss.x, rr.x), fmaf(-al, ss.y, rr.y));
+    r[j] = rn;
+    acc += (double)rn.x * rn.x + (double)rn.y * rn.y;
   }
   double tot;
-  if (reduce_last_block<1>(&acc, partials + kCntRho * 2 * kMaxPartials, &sc->counter[kCntRho], &tot)) {
-    sc->beta = (sc->rho > 0.0) ? tot / sc->rho : 0.0;
-    sc->rho = tot;
-    sc->cg_res = sqrt(tot);
-  }
+  if (reduce_last_block<1>(&acc, partials + kCntRho * 2 * kMaxPartials, &sc->counter[kCntRho], &tot))
+    sc->cg_res = sqrt(tot);  // recurrence residual after the last update
 }
 
-// r = b - Qx; p = r; rho = ||r||^2 (the start of purify_cg_solve).
+// r = b - Qx (the start of purify_cg_solve); the next Q-epilogue starts the solve.
 __global__ void k_cg_residual_init(int64_t n, const float2* __restrict__ b, const float2* __restrict__ qx,
-                                   float2* __restrict__ r, float2* __restrict__ p, double* partials,
-                                   DevScalars* sc) {
-  double acc = 0.0;
-  GRID_STRIDE(j, n) {
-    const float2 v = csub(b[j], qx[j]);
-    r[j] = v;
-    p[j] = v;
-    acc += (double)v.x * v.x + (double)v.y * v.y;
-  }
-  double tot;
-  if (reduce_last_block<1>(&acc, partials + kCntRho0 * 2 * kMaxPartials, &sc->counter[kCntRho0], &tot)) {
-    sc->rho = tot;
-    sc->beta = 0.0;
-    sc->cg_res = sqrt(tot);
-  }
+                                   float2* __restrict__ r, DevScalars* sc) {
+  GRID_STRIDE(j, n) r[j] = csub(b[j], qx[j]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_first = 1;
 }
 
 // max |a_j| -> sc->amax
@@ -211,16 +205,15 @@ int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s
   return check_cuda(cudaGetLastError());
 }
 
-int launch_cg_update(purify_ctx* c, float2* x, float2* r, const float2* p, const float2* qp, cudaStream_t s) {
+int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, cudaStream_t s) {
   const int64_t N = (int64_t)c->n * c->n;
-  PURIFY_LAUNCH(c, "cg_update", s, (k_cg_update<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, qp, c->d_partials, c->d_sc)));
+  PURIFY_LAUNCH(c, "cg_apply", s, (k_cg_apply<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, sv, w, c->d_partials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 
-int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, float2* p,
-                            cudaStream_t s) {
+int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, cudaStream_t s) {
   const int64_t N = (int64_t)c->n * c->n;
-  PURIFY_LAUNCH(c, "cg_residual_init", s, (k_cg_residual_init<<<blocks_for(N), 256, 0, s>>>(N, b, qx, r, p, c->d_partials, c->d_sc)));
+  PURIFY_LAUNCH(c, "cg_residual_init", s, (k_cg_residual_init<<<blocks_for(N), 256, 0, s>>>(N, b, qx, r, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 

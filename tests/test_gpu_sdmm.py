@@ -175,7 +175,7 @@ def test_profiler_and_launch_counter():
     prof = ctx.profile_collect()
     ctx.profile_enable(False)
     names = {r[0] for r in prof}
-    assert {"row_fwd", "col_fwd", "degrid", "grid", "col_inv", "row_inv", "cg_update", "dwt_level",
+    assert {"row_fwd", "col_fwd", "degrid", "grid", "col_inv", "row_inv", "dwt_level",
             "idwt_level", "sdmm_l2"} <= names
     assert sum(r[1] for r in prof) == per_step
     assert all(r[2] > 0 for r in prof)
