@@ -158,6 +158,7 @@ FftPlan make_plan(int L) {
     if (rest % 2 == 0) { p.radix[p.nst++] = 2; rest /= 2; }
   }
   if (rest != 1) p.nst = -1;
+  else finish_plan(p);
   return p;
 }
 

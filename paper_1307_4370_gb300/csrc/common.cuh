@@ -77,13 +77,58 @@ __device__ __forceinline__ int wrap(int k, int L) {
 }
 
 // ---------------------------------------------------------------------------
+// Division by a divisor of the form 2^sh or 3 * 2^sh without an integer
+// divide: q = x >> sh, then q / 3 as the high half of q * ceil(2^33 / 3).
+// Every index split in the FFT passes (by L, n, the signal count, L/R and
+// the Stockham span Ns) has this form.
+// ---------------------------------------------------------------------------
+struct Div {
+  int d;
+  int sh;
+  int three;
+};
+
+__host__ __device__ inline Div make_div(int d) {
+  Div v{d, 0, 0};
+  int r = d;
+  if (r % 3 == 0) {
+    v.three = 1;
+    r /= 3;
+  }
+  while (r > 1) {
+    r >>= 1;
+    ++v.sh;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int udiv(int x, const Div& v) {
+  const unsigned q = (unsigned)x >> v.sh;
+  return v.three ? (int)(__umulhi(q, 0xAAAAAAABu) >> 1) : (int)q;
+}
+
+// ---------------------------------------------------------------------------
 // FFT plan: Stockham stages with radices in {2, 3, 4, 8}.
 // ---------------------------------------------------------------------------
 struct FftPlan {
   int L;
   int nst;
   int radix[24];
+  Div ns[24];   // Ns of each stage (product of the earlier radices)
+  Div lr[24];   // L / R of each stage
+  Div divL;
 };
+
+// Fill the per-stage divisors of a plan whose radix list is set.
+inline void finish_plan(FftPlan& p) {
+  int ns = 1;
+  for (int st = 0; st < p.nst; ++st) {
+    p.ns[st] = make_div(ns);
+    p.lr[st] = make_div(p.L / p.radix[st]);
+    ns *= p.radix[st];
+  }
+  p.divL = make_div(p.L);
+}
 
 // ---------------------------------------------------------------------------
 // Daubechies filters (db1..db8), generated on the host at library load.

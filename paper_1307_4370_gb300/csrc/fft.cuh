@@ -79,42 +79,50 @@ struct SigLayout {
 // One Stockham stage over all signals held by the CTA.  Each thread owns
 // EPT / R butterflies; butterfly b maps to (signal, j) either signal-fastest
 // (SIG_FAST, for column transforms where signals are adjacent in memory) or
-// element-fastest.  nsig * L == blockDim.x * EPT.
+// element-fastest.  Butterflies beyond nsig * L / R (when the CTA has more
+// threads than the signals need) are skipped.
 template <int R, int EPT, bool SIG_FAST>
-__device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L, int Ns, int nsig,
-                                               const float2* tw) {
+__device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L, const Div& ns, const Div& lr,
+                                               const Div& dsig, int nsig, const float2* tw) {
   static_assert(EPT % R == 0, "radix must divide elements per thread");
   constexpr int NB = EPT / R;
   const int nthr = blockDim.x;
-  const int LR = L / R;
+  const int LR = lr.d;
+  const int Ns = ns.d;
+  const int nbfly = nsig * LR;
   const int twstep = L / (Ns * R);
   float2 v[EPT];
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     const int b = threadIdx.x + k * nthr;
-    int s, j;
-    if (SIG_FAST) { s = b % nsig; j = b / nsig; }
-    else { j = b % LR; s = b / LR; }
-    const int kk = j % Ns;
+    if (b < nbfly) {
+      int s, j;
+      if (SIG_FAST) { j = udiv(b, dsig); s = b - j * nsig; }
+      else { s = udiv(b, lr); j = b - s * LR; }
+      const int kk = j - udiv(j, ns) * Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[k * R + r] = buf[lay.at(s, j + r * LR)];
-    if (Ns > 1) {
+      for (int r = 0; r < R; ++r) v[k * R + r] = buf[lay.at(s, j + r * LR)];
+      if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], tw[r * kk * twstep]);
+        for (int r = 1; r < R; ++r) v[k * R + r] = cmul(v[k * R + r], tw[r * kk * twstep]);
+      }
+      dft_small<R>(&v[k * R]);
     }
-    dft_small<R>(&v[k * R]);
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     const int b = threadIdx.x + k * nthr;
-    int s, j;
-    if (SIG_FAST) { s = b % nsig; j = b / nsig; }
-    else { j = b % LR; s = b / LR; }
-    const int kk = j % Ns;
-    const int base = (j / Ns) * Ns * R + kk;
+    if (b < nbfly) {
+      int s, j;
+      if (SIG_FAST) { j = udiv(b, dsig); s = b - j * nsig; }
+      else { s = udiv(b, lr); j = b - s * LR; }
+      const int jq = udiv(j, ns);
+      const int kk = j - jq * Ns;
+      const int base = jq * Ns * R + kk;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[lay.at(s, base + r * Ns)] = v[k * R + r];
+      for (int r = 0; r < R; ++r) buf[lay.at(s, base + r * Ns)] = v[k * R + r];
+    }
   }
   __syncthreads();
 }
@@ -123,20 +131,22 @@ __device__ __forceinline__ void stockham_stage(float2* buf, SigLayout lay, int L
 template <int EPT, bool SIG_FAST>
 __device__ __forceinline__ void fft_smem(float2* buf, SigLayout lay, const FftPlan& plan, int nsig,
                                          const float2* __restrict__ tw) {
-  int Ns = 1;
+  const Div dsig = make_div(nsig);
   for (int st = 0; st < plan.nst; ++st) {
     const int R = plan.radix[st];
+    const Div& ns = plan.ns[st];
+    const Div& lr = plan.lr[st];
     if constexpr (EPT % 8 == 0) {
-      if (R == 8) { stockham_stage<8, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 8; continue; }
+      if (R == 8) { stockham_stage<8, EPT, SIG_FAST>(buf, lay, plan.L, ns, lr, dsig, nsig, tw); continue; }
     }
     if constexpr (EPT % 4 == 0) {
-      if (R == 4) { stockham_stage<4, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 4; continue; }
+      if (R == 4) { stockham_stage<4, EPT, SIG_FAST>(buf, lay, plan.L, ns, lr, dsig, nsig, tw); continue; }
     }
     if constexpr (EPT % 3 == 0) {
-      if (R == 3) { stockham_stage<3, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 3; continue; }
+      if (R == 3) { stockham_stage<3, EPT, SIG_FAST>(buf, lay, plan.L, ns, lr, dsig, nsig, tw); continue; }
     }
     if constexpr (EPT % 2 == 0) {
-      if (R == 2) { stockham_stage<2, EPT, SIG_FAST>(buf, lay, plan.L, Ns, nsig, tw); Ns *= 2; continue; }
+      if (R == 2) { stockham_stage<2, EPT, SIG_FAST>(buf, lay, plan.L, ns, lr, dsig, nsig, tw); continue; }
     }
   }
 }

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
                           const DevScalars* __restrict__ sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  const Div dsig = make_div(nsig), dn = make_div(n);
   float2* tws = sm + nsig * L;  // twiddles staged next to the signals
   for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int r0 = blockIdx.x * nsig;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
     first = sc->upd_first != 0;
   }
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = idx / L, e = idx - s * L;
+    const int s = udiv(idx, plan.divL), e = idx - s * L;
     const int r = r0 + s;
     int cc = e + (n >> 1);
     if (cc >= L) cc -= L;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restric
   __syncthreads();
   fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = idx / L, e = idx - s * L;
+    const int s = udiv(idx, plan.divL), e = idx - s * L;
     half[(size_t)(r0 + s) * L + e] = sm[s * L + e];
   }
 }
@@ -132,11 +133,12 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
                           const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  const Div dsig = make_div(nsig), dn = make_div(n);
   float2* tws = sm + nsig * L;  // twiddles staged next to the signals
   for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int c0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = idx / nsig, s = idx - e * nsig;
+    const int e = udiv(idx, dsig), s = idx - e * nsig;
     int r = e + (n >> 1);
     if (r >= L) r -= L;
     sm[e * nsig + s] = (r < n) ? half[(size_t)r * L + c0 + s] : make_float2(0.f, 0.f);
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
   __syncthreads();
   fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = idx / nsig, s = idx - e * nsig;
+    const int e = udiv(idx, dsig), s = idx - e * nsig;
     X[(size_t)e * L + c0 + s] = sm[e * nsig + s];
   }
 }
@@ -165,12 +167,14 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
   const int4 ch = dchunks[blockIdx.x];
   const int tr = ch.x / tiles_1d, tc = ch.x - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
-  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-    const int rr = idx / W, cc = idx - rr * W;
-    int r = R0 + rr, c = C0 + cc;
+  for (int rr = threadIdx.x >> 5; rr < W; rr += blockDim.x >> 5) {
+    int r = R0 + rr;
     if (r >= L) r -= L;
-    if (c >= L) c -= L;
-    halo[idx] = __ldg(&X[(size_t)r * L + c]);
+    for (int cc = threadIdx.x & 31; cc < W; cc += 32) {
+      int c = C0 + cc;
+      if (c >= L) c -= L;
+      halo[rr * W + cc] = __ldg(&X[(size_t)r * L + c]);
+    }
   }
   __syncthreads();
   double acc2[2] = {0.0, 0.0};
@@ -310,15 +314,12 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
     }
   }
   __syncthreads();
-  // off[k] = first entry with key >= k (entries are sorted by key)
-  for (int k = threadIdx.x; k <= NK; k += blockDim.x) {
-    int lo = 0, hi = ne;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (key[mid] < k) lo = mid + 1;
-      else hi = mid;
-    }
-    off[k] = lo;
+  // off[k] = first entry with key >= k: entries are sorted by key, so entry e
+  // fills the keys after its predecessor's up to its own (the end fills the rest)
+  for (int e = threadIdx.x; e <= ne; e += blockDim.x) {
+    const int kprev = (e == 0) ? -1 : key[e - 1];
+    const int kcur = (e == ne) ? NK : key[e];
+    for (int k = kprev + 1; k <= kcur; ++k) off[k] = e;
   }
   __syncthreads();
   const int HB = T / 2;
@@ -385,17 +386,18 @@ __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, 
                           const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  const Div dsig = make_div(nsig), dn = make_div(n);
   float2* tws = sm + nsig * L;  // twiddles staged next to the signals
   for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int c0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = idx / nsig, s = idx - e * nsig;
+    const int e = udiv(idx, dsig), s = idx - e * nsig;
     sm[e * nsig + s] = cconj(X[(size_t)e * L + c0 + s]);
   }
   __syncthreads();
   fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
-    const int r = idx / nsig, s = idx - r * nsig;
+    const int r = udiv(idx, dsig), s = idx - r * nsig;
     int e = r - (n >> 1);
     if (e < 0) e += L;
     half[(size_t)r * L + c0 + s] = cconj(sm[e * nsig + s]);
@@ -418,11 +420,12 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
                           double* partials, DevScalars* sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
+  const Div dsig = make_div(nsig), dn = make_div(n);
   float2* tws = sm + nsig * L;  // twiddles staged next to the signals
   for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int r0 = blockIdx.x * nsig;
   for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = idx / L, e = idx - s * L;
+    const int s = udiv(idx, plan.divL), e = idx - s * L;
     sm[s * L + e] = cconj(half[(size_t)(r0 + s) * L + e]);
   }
   __syncthreads();
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
   const float invL = 1.0f / (float)L;
   double acc[2] = {0.0, 0.0};
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
-    const int s = idx / n, c = idx - s * n;
+    const int s = udiv(idx, dn), c = idx - s * n;
     const int r = r0 + s;
     int e = c - (n >> 1);
     if (e < 0) e += L;

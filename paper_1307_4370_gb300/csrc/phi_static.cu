@@ -128,7 +128,9 @@ bool st_plan(int L, FftPlan& p) {
     if (rest % 4 == 0) { p.radix[p.nst++] = 4; rest /= 4; }
     if (rest % 2 == 0) { p.radix[p.nst++] = 2; rest /= 2; }
   }
-  return rest == 1;
+  if (rest != 1) return false;
+  finish_plan(p);
+  return true;
 }
 
 // Twiddles exp(-2 pi i m / L) and 1 / g_hat((r - n/2) / L), in double.

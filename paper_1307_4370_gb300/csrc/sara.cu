@@ -105,15 +105,21 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   float2* rowp = sm + RH * RH;       // RH x 2TI  ([a | d] per input row)
   load_filters(wf, p, h, g);
   const float2* src = in_shared ? in : in + (size_t)k * (G.n / 2) * (G.n / 2);
-  for (int idx = threadIdx.x; idx < RH * RH; idx += blockDim.x) {
-    const int rr = idx / RH, cc = idx - rr * RH;
-    const int r = (2 * I1 + rr) % L, c = (2 * I2 + cc) % L;
-    inb[idx] = src[(size_t)r * L + c];
+  const Div dL = make_div(L), dTI = make_div(TI), d2TI = make_div(2 * TI);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int rr = threadIdx.x >> 5; rr < RH; rr += nw) {
+    int r = 2 * I1 + rr;
+    r -= udiv(r, dL) * L;
+    for (int cc = lane; cc < RH; cc += 32) {
+      int c = 2 * I2 + cc;
+      c -= udiv(c, dL) * L;
+      inb[rr * RH + cc] = src[(size_t)r * L + c];
+    }
   }
   __syncthreads();
   // rows: a[i2] = sum_m h[m] s[2 i2 + m], d[i2] = sum_m g[m] s[2 i2 + m]
   for (int idx = threadIdx.x; idx < RH * TI; idx += blockDim.x) {
-    const int rr = idx / TI, i2 = idx - rr * TI;
+    const int rr = udiv(idx, dTI), i2 = idx - rr * TI;
     const float2* s = inb + rr * RH + 2 * i2;
     float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
     for (int m = 0; m < taps; ++m) {
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
   double f1 = 0.0;
   for (int idx = threadIdx.x; idx < TI * 2 * TI; idx += blockDim.x) {
-    const int i1 = idx / (2 * TI), kc = idx - i1 * (2 * TI);
+    const int i1 = udiv(idx, d2TI), kc = idx - i1 * (2 * TI);
     float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
     for (int m = 0; m < taps; ++m) {
       const float2 v = rowp[(2 * i1 + m) * (2 * TI) + kc];
@@ -206,6 +212,8 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   const int kend = G.last ? G.nb : blockIdx.z + 1;
   float2 accum[16];  // up to (2TO)^2 / blockDim outputs per thread: 1024 / 256 = 4 (<= 16 for safety)
   const int nout = (2 * TO) * (2 * TO);
+  const Div dH = make_div(H), d2TO = make_div(2 * TO);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = 0; t < 16; ++t) accum[t] = make_float2(0.f, 0.f);
   for (int k = kbeg; k < kend; ++k) {
     const int p = bl.p[k];
@@ -223,19 +231,25 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     const float2* llsrc = ll_from_plane ? plane : ll_in + (size_t)k * (G.n / 2) * (G.n / 2);
     const int llstride = ll_from_plane ? G.n : H;
     // window origin: coefficient K/2 - p + 1 (mod H)
-    const int o1 = K1 / 2 - p + 1, o2 = K2 / 2 - p + 1;
-    for (int idx = threadIdx.x; idx < CW * CW; idx += blockDim.x) {
-      const int t1 = idx / CW, t2 = idx - t1 * CW;
-      const int c1 = wrap(o1 + t1, H), c2 = wrap(o2 + t2, H);
-      LLs[idx] = llsrc[(size_t)c1 * llstride + c2];
-      HLs[idx] = plane[(size_t)(H + c1) * G.n + c2];
-      LHs[idx] = plane[(size_t)c1 * G.n + H + c2];
-      HHs[idx] = plane[(size_t)(H + c1) * G.n + H + c2];
+    const int o1 = K1 / 2 - p + 1 + 8 * H, o2 = K2 / 2 - p + 1 + 8 * H;  // shifted to stay >= 0
+    for (int t1 = threadIdx.x >> 5; t1 < CW; t1 += nw) {
+      int c1 = o1 + t1;
+      c1 -= udiv(c1, dH) * H;
+      for (int t2 = lane; t2 < CW; t2 += 32) {
+        int c2 = o2 + t2;
+        c2 -= udiv(c2, dH) * H;
+        const int idx = t1 * CW + t2;
+        LLs[idx] = llsrc[(size_t)c1 * llstride + c2];
+        HLs[idx] = plane[(size_t)(H + c1) * G.n + c2];
+        LHs[idx] = plane[(size_t)c1 * G.n + H + c2];
+        HHs[idx] = plane[(size_t)(H + c1) * G.n + H + c2];
+      }
     }
     __syncthreads();
     // column synthesis: output row kappa1 in [0, 2TO), window column t2
-    for (int idx = threadIdx.x; idx < 2 * TO * CW; idx += blockDim.x) {
-      const int k1 = idx / CW, t2 = idx - k1 * CW;
+    for (int t2 = threadIdx.x >> 5; t2 < CW; t2 += nw)
+    for (int k1 = lane; k1 < 2 * TO; k1 += 32) {
+      const int idx = k1 * CW + t2;
       float2 av = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
       for (int m = (k1 & 1); m < taps; m += 2) {
         const int t1 = (k1 - m) / 2 + p - 1;  // k1 - m even
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     // row synthesis
     int t = 0;
     for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
-      const int k1 = idx / (2 * TO), k2 = idx - k1 * (2 * TO);
+      const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
       float2 s = make_float2(0.f, 0.f);
       for (int m = (k2 & 1); m < taps; m += 2) {
         const int t2 = (k2 - m) / 2 + p - 1;
@@ -272,7 +286,7 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   if (G.last) {
     int t = 0;
     for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
-      const int k1 = idx / (2 * TO), k2 = idx - k1 * (2 * TO);
+      const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
       const int gk1 = K1 + k1, gk2 = K2 + k2;
       if (gk1 < L && gk2 < L) {
         float2 s = accum[t];
