@@ -160,6 +160,7 @@ struct DevScalars {
   double pqp;        // <p, Qp>
   double l2_dn2;     // ||s2 + z2 - y||^2
   double l2_res2;    // ||s2 - y||^2
+  double l2_scale;   // min(1, eps / ||s2 + z2 - y||)
   double f1;         // sum w |Psi^H x|
   double f1_prev;
   double amax;       // max |.| reductions

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
     }
   }
   __syncthreads();
-  double acc2[2] = {0.0, 0.0};
+  float part[2] = {0.f, 0.f};  // per-thread sums of at most a few terms; FP64 across threads
   for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
     const float2 u = __ldg(&uv[i]);
     int k0r, k0c;
@@ -237,20 +237,22 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
         y = make_float2(__uint_as_float(bits << 16) * sc4, __uint_as_float(bits & 0xffff0000u) * sc4);
       }
       const float2 z = a.z2[i];
-      const double dx = (double)acc.x + (double)z.x - (double)y.x;
-      const double dy = (double)acc.y + (double)z.y - (double)y.y;
-      const double ex = (double)acc.x - (double)y.x;
-      const double ey = (double)acc.y - (double)y.y;
-      acc2[0] += dx * dx + dy * dy;
-      acc2[1] += ex * ex + ey * ey;
+      const float2 av = cadd(acc, z);
+      const float dx = av.x - y.x, dy = av.y - y.y;    // a - y, y close to a: nearly exact
+      const float ex = acc.x - y.x, ey = acc.y - y.y;
+      part[0] = fmaf(dx, dx, fmaf(dy, dy, part[0]));
+      part[1] = fmaf(ex, ex, fmaf(ey, ey, part[1]));
     }
   }
   if (MODE == kDegridSdmm) {
+    double acc2[2] = {(double)part[0], (double)part[1]};
     double tot[2];
     if (reduce_last_block<2>(acc2, partials + kCntL2 * 2 * kMaxPartials, &sc->counter[kCntL2], tot)) {
       sc->l2_dn2 = tot[0];
       sc->l2_res2 = tot[1];
       sc->nu = sqrt(tot[1]) / sc->eps;
+      const double nd = sqrt(tot[0]);
+      sc->l2_scale = (nd > sc->eps) ? sc->eps / nd : 1.0;  // projection factor of the l2 ball
     }
   }
 }
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
   __syncthreads();
   fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
   const float invL = 1.0f / (float)L;
-  double acc[2] = {0.0, 0.0};
+  float part[2] = {0.f, 0.f};  // per-thread sums of a few terms; FP64 across threads
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
     const int s = udiv(idx, dn), c = idx - s * n;
     const int r = r0 + s;
@@ -446,8 +448,8 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
       const float2 p = a.p[off];
       const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
       a.out[off] = q;
-      acc[0] += (double)p.x * (double)p.x + (double)p.y * (double)p.y;  // <r, r>
-      acc[1] += (double)p.x * (double)q.x + (double)p.y * (double)q.y;  // Re <w, r>
+      part[0] = fmaf(p.x, p.x, fmaf(p.y, p.y, part[0]));  // <r, r>
+      part[1] = fmaf(p.x, q.x, fmaf(p.y, q.y, part[1]));  // Re <w, r>
     } else {
       const float2 xh = a.p[off];
       const float2 z3 = a.z3[off];
@@ -464,6 +466,7 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
     }
   }
   if (MODE == kRowOutCgQ) {
+    double acc[2] = {(double)part[0], (double)part[1]};
     double tot[2];
     if (reduce_last_block<2>(acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], tot)) {
       const double gamma = tot[0], delta = tot[1];

@@ -45,8 +45,10 @@ __device__ __forceinline__ void load_filters(const WaveletFilters& wf, int p, fl
   }
 }
 
-// Soft threshold + dual update for one final coefficient alpha at index j.
-__device__ __forceinline__ double sara_prox(float2 al, size_t j, const SaraProxArgs& pa, float gamma) {
+// Soft threshold + dual update for one final coefficient alpha at index j;
+// returns w |alpha| (its term of f1), summed per thread in FP32 (a few terms)
+// and across threads in FP64.
+__device__ __forceinline__ float sara_prox(float2 al, size_t j, const SaraProxArgs& pa, float gamma) {
   const float w = pa.w ? pa.w[j] : 1.0f;
   const float2 z = pa.z1[j];
   const float2 a = cadd(al, z);
@@ -57,7 +59,7 @@ __device__ __forceinline__ double sara_prox(float2 al, size_t j, const SaraProxA
   const float2 z1n = csub(a, r1);
   pa.z1[j] = z1n;
   pa.u1[j] = csub(r1, z1n);
-  return (double)w * sqrt((double)al.x * al.x + (double)al.y * al.y);
+  return w * sqrtf(fmaf(al.x, al.x, al.y * al.y));
 }
 
 // ---------------------------------------------------------------------------
@@ -66,7 +68,7 @@ __device__ __forceinline__ double sara_prox(float2 al, size_t j, const SaraProxA
 template <int MODE>
 __global__ void k_dirac(const float2* __restrict__ x, float2* __restrict__ alpha, int64_t N, float scale,
                         SaraProxArgs pa, double* partials, DevScalars* sc) {
-  double f1 = 0.0;
+  float f1 = 0.f;
   const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
     const float2 al = cscale(x[j], scale);
@@ -74,8 +76,8 @@ __global__ void k_dirac(const float2* __restrict__ x, float2* __restrict__ alpha
     else f1 += sara_prox(al, (size_t)j, pa, gamma);
   }
   if (MODE == kSaraProx) {
-    double tot;
-    if (reduce_last_block<1>(&f1, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot))
+    double f1d = (double)f1, tot;
+    if (reduce_last_block<1>(&f1d, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot))
       sc->f1 = tot;  // first contribution of this analysis
   }
 }
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   float2* plane = coef + (size_t)(G.plane0 + k) * G.n * G.n;
   float2* llk = ll_out + (size_t)k * (G.n / 2) * (G.n / 2);
   const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
-  double f1 = 0.0;
+  float f1 = 0.f;
   for (int idx = threadIdx.x; idx < TI * 2 * TI; idx += blockDim.x) {
     const int i1 = udiv(idx, d2TI), kc = idx - i1 * (2 * TI);
     float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
@@ -177,8 +179,8 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
     }
   }
   if (MODE == kSaraProx) {
-    double tot;
-    if (reduce_last_block<1>(&f1, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot)) {
+    double f1d = (double)f1, tot;
+    if (reduce_last_block<1>(&f1d, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot)) {
       sc->f1 += tot;
       if (G.last) {
         // halting quantity zeta of §4.4 (after the last contribution)

@@ -37,12 +37,12 @@ __global__ void k_soft(int64_t n, const float2* __restrict__ in, const float* __
 // ||a - b||^2 in FP64 -> sc->norm2
 __global__ void k_norm_diff(int64_t n, const float2* __restrict__ a, const float2* __restrict__ b,
                             double* partials, DevScalars* sc) {
-  double acc = 0.0;
+  float part = 0.f;  // per-thread FP32 sum of a few terms; FP64 across threads
   GRID_STRIDE(j, n) {
-    const double dx = (double)a[j].x - (double)b[j].x, dy = (double)a[j].y - (double)b[j].y;
-    acc += dx * dx + dy * dy;
+    const float dx = a[j].x - b[j].x, dy = a[j].y - b[j].y;
+    part = fmaf(dx, dx, fmaf(dy, dy, part));
   }
-  double tot;
+  double acc = (double)part, tot;
   if (reduce_last_block<1>(&acc, partials + kCntNorm * 2 * kMaxPartials, &sc->counter[kCntNorm], &tot))
     sc->norm2 = tot;
 }
@@ -50,8 +50,13 @@ __global__ void k_norm_diff(int64_t n, const float2* __restrict__ a, const float
 // Projection onto {r : ||r - y|| <= eps} given ||in - y||^2 on the device.
 __global__ void k_l2_project(int64_t n, const float2* __restrict__ in, const float2* __restrict__ y, double eps,
                              const double* norm2, float2* __restrict__ out) {
-  const double nd = sqrt(*norm2);
-  const float scale = (nd > eps) ? (float)(eps / nd) : 1.0f;
+  __shared__ float s_scale;  // one FP64 square root per block
+  if (threadIdx.x == 0) {
+    const double nd = sqrt(*norm2);
+    s_scale = (nd > eps) ? (float)(eps / nd) : 1.0f;
+  }
+  __syncthreads();
+  const float scale = s_scale;
   GRID_STRIDE(j, n) {
     const float2 yy = y[j], r = in[j];
     out[j] = make_float2(fmaf(scale, r.x - yy.x, yy.x), fmaf(scale, r.y - yy.y, yy.y));
@@ -70,7 +75,7 @@ __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict
                            float2* __restrict__ sv, const float2* __restrict__ w, double* partials, DevScalars* sc) {
   const float al = (float)sc->alpha, be = (float)sc->beta;
   const bool first = sc->upd_first != 0;
-  double acc = 0.0;
+  float part = 0.f;
   GRID_STRIDE(j, n) {
     const float2 rr = r[j], ww = w[j];
     float2 pp, ss;
@@ -86,9 +91,9 @@ __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict
     x[j] = make_float2(fmaf(al, pp.x, x[j].x), fmaf(al, pp.y, x[j].y));
     const float2 rn = make_float2(fmaf(-al, ss.x, rr.x), fmaf(-al, ss.y, rr.y));
     r[j] = rn;
-    acc += (double)rn.x * rn.x + (double)rn.y * rn.y;
+    part = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, part));
   }
-  double tot;
+  double acc = (double)part, tot;
   if (reduce_last_block<1>(&acc, partials + kCntRho * 2 * kMaxPartials, &sc->counter[kCntRho], &tot))
     sc->cg_res = sqrt(tot);  // recurrence residual after the last update
 }
@@ -102,9 +107,9 @@ __global__ void k_cg_residual_init(int64_t n, const float2* __restrict__ b, cons
 
 // max |a_j| -> sc->amax
 __global__ void k_max_abs(int64_t n, const float2* __restrict__ a, double* partials, DevScalars* sc) {
-  double m = 0.0;
-  GRID_STRIDE(j, n) m = fmax(m, sqrt((double)a[j].x * a[j].x + (double)a[j].y * a[j].y));
-  double tot;
+  float mf = 0.f;
+  GRID_STRIDE(j, n) mf = fmaxf(mf, sqrtf(fmaf(a[j].x, a[j].x, a[j].y * a[j].y)));
+  double m = (double)mf, tot;
   if (reduce_last_block<1, true>(&m, partials + kCntMax * 2 * kMaxPartials, &sc->counter[kCntMax], &tot))
     sc->amax = tot;
 }
@@ -116,8 +121,7 @@ __global__ void k_max_abs(int64_t n, const float2* __restrict__ a, double* parti
 __global__ void k_sdmm_l2(int64_t M, const float2* __restrict__ s2, float2* __restrict__ z2,
                           const float2* __restrict__ y, const uint16_t* __restrict__ yb,
                           const float* __restrict__ yscale, float2* __restrict__ v, const DevScalars* sc) {
-  const double nd = sqrt(sc->l2_dn2);
-  const float scale = (nd > sc->eps) ? (float)(sc->eps / nd) : 1.0f;
+  const float scale = (float)sc->l2_scale;
   GRID_STRIDE(i, M) {
     float2 yy;
     if (y) {
@@ -140,13 +144,13 @@ __global__ void k_sdmm_l2(int64_t M, const float2* __restrict__ s2, float2* __re
 __global__ void k_reweight(int64_t n, const float2* __restrict__ alpha, float* __restrict__ w, int round,
                            const DevScalars* sc) {
   const double amax = sc->amax;
-  const double delta = fmax(pow(10.0, -(double)round) * amax, 1e-6 * amax);
+  const float delta = (float)fmax(pow(10.0, -(double)round) * amax, 1e-6 * amax);
   GRID_STRIDE(j, n) {
-    if (delta == 0.0) {
+    if (delta == 0.f) {
       w[j] = 1.0f;
     } else {
-      const double a = sqrt((double)alpha[j].x * alpha[j].x + (double)alpha[j].y * alpha[j].y);
-      w[j] = (float)(delta / (delta + a));
+      const float a = sqrtf(fmaf(alpha[j].x, alpha[j].x, alpha[j].y * alpha[j].y));
+      w[j] = delta / (delta + a);
     }
   }
 }
