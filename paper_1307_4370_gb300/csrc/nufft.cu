@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
     }
   }
   __syncthreads();
-  float part[2] = {0.f, 0.f};  // per-thread sums of at most a few terms; FP64 across threads
+  FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
   for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
     const float2 u = __ldg(&uv[i]);
     int k0r, k0c;
@@ -238,14 +238,14 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
       }
       const float2 z = a.z2[i];
       const float2 av = cadd(acc, z);
-      const float dx = av.x - y.x, dy = av.y - y.y;    // a - y, y close to a: nearly exact
-      const float ex = acc.x - y.x, ey = acc.y - y.y;
-      part[0] = fmaf(dx, dx, fmaf(dy, dy, part[0]));
-      part[1] = fmaf(ex, ex, fmaf(ey, ey, part[1]));
+      part[0].add_sq_diff(av.x, y.x);
+      part[0].add_sq_diff(av.y, y.y);
+      part[1].add_sq_diff(acc.x, y.x);
+      part[1].add_sq_diff(acc.y, y.y);
     }
   }
   if (MODE == kDegridSdmm) {
-    double acc2[2] = {(double)part[0], (double)part[1]};
+    double acc2[2] = {part[0].value(), part[1].value()};
     double tot[2];
     if (reduce_last_block<2>(acc2, partials + kCntL2 * 2 * kMaxPartials, &sc->counter[kCntL2], tot)) {
       sc->l2_dn2 = tot[0];
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
   __syncthreads();
   fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
   const float invL = 1.0f / (float)L;
-  float part[2] = {0.f, 0.f};  // per-thread sums of a few terms; FP64 across threads
+  FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
   for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
     const int s = udiv(idx, dn), c = idx - s * n;
     const int r = r0 + s;
@@ -448,8 +448,10 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
       const float2 p = a.p[off];
       const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
       a.out[off] = q;
-      part[0] = fmaf(p.x, p.x, fmaf(p.y, p.y, part[0]));  // <r, r>
-      part[1] = fmaf(p.x, q.x, fmaf(p.y, q.y, part[1]));  // Re <w, r>
+      part[0].add_prod(p.x, p.x);  // <r, r>
+      part[0].add_prod(p.y, p.y);
+      part[1].add_prod(p.x, q.x);  // Re <w, r>
+      part[1].add_prod(p.y, q.y);
     } else {
       const float2 xh = a.p[off];
       const float2 z3 = a.z3[off];
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ hal
     }
   }
   if (MODE == kRowOutCgQ) {
-    double acc[2] = {(double)part[0], (double)part[1]};
+    double acc[2] = {part[0].value(), part[1].value()};
     double tot[2];
     if (reduce_last_block<2>(acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], tot)) {
       const double gamma = tot[0], delta = tot[1];

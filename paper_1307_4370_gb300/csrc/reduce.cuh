@@ -10,6 +10,39 @@
 
 namespace purify {
 
+// ---------------------------------------------------------------------------
+// Per-thread accumulation without FP64 arithmetic (GB300 has little FP64
+// throughput): terms are formed exactly with error-free transformations
+// (TwoSum for a difference, an FMA for a product's rounding error) and summed
+// into a float pair (hi, lo); the pair goes to FP64 once per thread, and the
+// sums across threads and blocks are FP64.  With the few terms each thread
+// holds, the per-thread error is far below FP64 rounding of the total.
+// ---------------------------------------------------------------------------
+struct FPair {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float p, float pe) {  // += p + pe
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e + pe;
+  }
+  // += x * y (exact product)
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = x * y;
+    add(p, fmaf(x, y, -p));
+  }
+  // += (a - b)^2 with a - b formed exactly
+  __device__ __forceinline__ void add_sq_diff(float a, float b) {
+    const float d = a - b;
+    const float bb = d - a;
+    const float de = (a - (d - bb)) + (-b - bb);
+    const float p = d * d;
+    add(p, fmaf(d, d, -p) + 2.f * d * de);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Tree over the first `valid` lanes of a warp whose first `present` lanes
 // exist (any block size, including a partial last warp); every present lane
 // calls it, and the result is valid in lane 0.

@@ -37,12 +37,12 @@ __global__ void k_soft(int64_t n, const float2* __restrict__ in, const float* __
 // ||a - b||^2 in FP64 -> sc->norm2
 __global__ void k_norm_diff(int64_t n, const float2* __restrict__ a, const float2* __restrict__ b,
                             double* partials, DevScalars* sc) {
-  float part = 0.f;  // per-thread FP32 sum of a few terms; FP64 across threads
+  FPair part;  // per-thread exact sum of a few terms; FP64 across threads
   GRID_STRIDE(j, n) {
-    const float dx = a[j].x - b[j].x, dy = a[j].y - b[j].y;
-    part = fmaf(dx, dx, fmaf(dy, dy, part));
+    part.add_sq_diff(a[j].x, b[j].x);
+    part.add_sq_diff(a[j].y, b[j].y);
   }
-  double acc = (double)part, tot;
+  double acc = part.value(), tot;
   if (reduce_last_block<1>(&acc, partials + kCntNorm * 2 * kMaxPartials, &sc->counter[kCntNorm], &tot))
     sc->norm2 = tot;
 }
@@ -75,7 +75,7 @@ __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict
                            float2* __restrict__ sv, const float2* __restrict__ w, double* partials, DevScalars* sc) {
   const float al = (float)sc->alpha, be = (float)sc->beta;
   const bool first = sc->upd_first != 0;
-  float part = 0.f;
+  FPair part;
   GRID_STRIDE(j, n) {
     const float2 rr = r[j], ww = w[j];
     float2 pp, ss;
@@ -91,9 +91,10 @@ __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict
     x[j] = make_float2(fmaf(al, pp.x, x[j].x), fmaf(al, pp.y, x[j].y));
     const float2 rn = make_float2(fmaf(-al, ss.x, rr.x), fmaf(-al, ss.y, rr.y));
     r[j] = rn;
-    part = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, part));
+    part.add_prod(rn.x, rn.x);
+    part.add_prod(rn.y, rn.y);
   }
-  double acc = (double)part, tot;
+  double acc = part.value(), tot;
   if (reduce_last_block<1>(&acc, partials + kCntRho * 2 * kMaxPartials, &sc->counter[kCntRho], &tot))
     sc->cg_res = sqrt(tot);  // recurrence residual after the last update
 }
