@@ -89,7 +89,12 @@ typedef enum {
  *   J           Kaiser-Bessel support per axis: 2, 4, 6 or 8.
  *   oversample  must be 2 (§6 uses k = 2; the grid is 2n x 2n).
  *   levels      wavelet levels of each Daubechies basis, 1..6 (4 in §6).
- *   bases_mask  bit 0 Dirac, bit p db_p (p = 1..8); SARA is 0x1FF.  */
+ *   bases_mask  bit 0 Dirac, bit p db_p (p = 1..8); SARA is 0x1FF.
+ *   tile        side of the grid tiles that organise G and G^T (a schedule
+ *               choice, not part of the method): 0 picks a default from the
+ *               grid size; otherwise 8, 16, 32 or 64, at least J and dividing
+ *               2n.  The autotuner of the Python package measures the
+ *               candidates.  */
 typedef struct {
   int32_t n;
   int64_t M;
@@ -97,6 +102,7 @@ typedef struct {
   int32_t oversample;
   int32_t levels;
   uint32_t bases_mask;
+  int32_t tile;
 } purify_desc;
 
 /* Create a context for one u-v coverage (§5: G depends only on the

@@ -37,7 +37,8 @@ class PurifyError(RuntimeError):
 
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("M", ctypes.c_int64), ("J", ctypes.c_int32),
-                ("oversample", ctypes.c_int32), ("levels", ctypes.c_int32), ("bases_mask", ctypes.c_uint32)]
+                ("oversample", ctypes.c_int32), ("levels", ctypes.c_int32), ("bases_mask", ctypes.c_uint32),
+                ("tile", ctypes.c_int32)]
 
 
 class SdmmParams(ctypes.Structure):
@@ -174,7 +175,7 @@ class Context:
     """
 
     def __init__(self, n: int, uv, J: int = 6, levels: int = 4, bases_mask: int = SARA_MASK,
-                 device=None):
+                 device=None, tile: int = 0):
         self.lib = load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -191,7 +192,8 @@ class Context:
         self.q = bin(self.bases_mask & 0x1FF).count("1")
         self.N = self.n * self.n
         self.D = self.q * self.N
-        desc = Desc(self.n, self.M, self.J, 2, self.levels, self.bases_mask)
+        self.tile = int(tile)
+        desc = Desc(self.n, self.M, self.J, 2, self.levels, self.bases_mask, self.tile)
         uv_keep = uv_t if uv_t.is_cuda else uv_t.numpy()
         self.ctx = purify_create(desc, _ptr(uv_keep))
 

@@ -473,6 +473,9 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   if (d->M < 1 || d->M > 2147483647LL) return PURIFY_E_SIZE;
   if (d->bases_mask == 0 || (d->bases_mask & ~0x1FFu)) return PURIFY_E_INVALID_ARG;
   if (!good_side(2 * d->n)) return PURIFY_E_UNSUPPORTED;
+  if (d->tile != 0 && ((d->tile != 8 && d->tile != 16 && d->tile != 32 && d->tile != 64) || d->tile < d->J ||
+                       (2 * d->n) % d->tile != 0))
+    return PURIFY_E_SIZE;
   cudaStream_t s = (cudaStream_t)stream;
   purify_ctx* c = new (std::nothrow) purify_ctx();
   if (!c) return PURIFY_E_ALLOC;
@@ -493,8 +496,12 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   c->plan = make_plan(c->L);
   if (c->plan.nst < 0) { delete c; return PURIFY_E_UNSUPPORTED; }
   make_daubechies(c->wf);
-  c->tileT = c->L >= 512 ? 32 : (c->L >= 64 ? 16 : 8);
-  while (c->tileT < c->J || c->L % c->tileT) c->tileT *= 2;
+  if (d->tile != 0) {
+    c->tileT = d->tile;
+  } else {
+    c->tileT = c->L >= 512 ? 32 : (c->L >= 64 ? 16 : 8);
+    while (c->tileT < c->J || c->L % c->tileT) c->tileT *= 2;
+  }
   c->tiles_1d = c->L / c->tileT;
   c->ntiles = c->tiles_1d * c->tiles_1d;
   const int64_t N = ctx_N(c), n2 = (int64_t)(c->n / 2) * (c->n / 2);

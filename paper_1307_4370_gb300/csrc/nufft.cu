@@ -316,12 +316,46 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
     }
   }
   __syncthreads();
-  // off[k] = first entry with key >= k: entries are sorted by key, so entry e
-  // fills the keys after its predecessor's up to its own (the end fills the rest)
-  for (int e = threadIdx.x; e <= ne; e += blockDim.x) {
-    const int kprev = (e == 0) ? -1 : key[e - 1];
-    const int kcur = (e == ne) ? NK : key[e];
-    for (int k = kprev + 1; k <= kcur; ++k) off[k] = e;
+  // off[k] = first entry with key >= k = number of entries with key < k:
+  // count the entries of each key, then an exclusive prefix sum over the keys
+  // (each thread owns a contiguous run of keys; balanced whatever the density)
+  for (int k = threadIdx.x; k <= NK; k += blockDim.x) off[k] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) atomicAdd(&off[key[e]], 1);
+  __syncthreads();
+  {
+    __shared__ int wsum[32];
+    const int per = (NK + 1 + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per, k1 = min(k0 + per, NK + 1);
+    int run = 0;
+    for (int k = k0; k < k1; ++k) run += off[k];
+    // exclusive scan of the runs across the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+      int v = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < nw) wsum[lane] = v;  // inclusive warp totals
+    }
+    __syncthreads();
+    int base = incl - run + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int k = k0; k < k1; ++k) {
+      const int cnt = off[k];
+      off[k] = base;
+      base += cnt;
+    }
   }
   __syncthreads();
   const int HB = T / 2;

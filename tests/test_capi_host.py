@@ -56,11 +56,12 @@ def test_default_params(lib):
     ("n", 7, -2), ("n", 20, -2), ("n", 4096 * 2, -2), ("J", 5, -2), ("J", 10, -2),
     ("oversample", 3, -2), ("levels", 0, -2), ("levels", 7, -2), ("M", 0, -2),
     ("bases_mask", 0, -1), ("bases_mask", 0x200, -1), ("n", 80, -7),
+    ("tile", 12, -2), ("tile", 2, -2), ("tile", 128, -2),
 ])
 def test_create_rejects_bad_descriptions(lib, field, value, code):
     from paper_1307_4370_gb300 import binding
 
-    d = binding.Desc(64, 100, 4, 2, 4, 0x1FF)
+    d = binding.Desc(64, 100, 4, 2, 4, 0x1FF, 0)
     setattr(d, field, value)
     if field == "n" and value == 80:
         d.levels = 4  # 80 = 16 * 5: 2n = 160 has the prime factor 5
@@ -74,7 +75,7 @@ def test_create_rejects_bad_descriptions(lib, field, value, code):
 def test_null_arguments(lib):
     from paper_1307_4370_gb300 import binding
 
-    d = binding.Desc(64, 100, 4, 2, 4, 0x1FF)
+    d = binding.Desc(64, 100, 4, 2, 4, 0x1FF, 0)
     assert lib.purify_create(None, ctypes.byref(d), None, None) == -1
     out = ctypes.c_void_p()
     assert lib.purify_create(ctypes.byref(out), None, None, None) == -1

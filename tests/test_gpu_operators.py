@@ -139,3 +139,26 @@ def test_cg_solve(n, M, J, iters):
     want, want_res = ocg.cg(lambda v: me.phi_adj(me.phi(v, uv, J), uv, n, J) + 2.0 * v, b, x0, iters)
     assert rel_err(host(x).reshape(n, n), want) <= 1e-5
     assert float(res.item()) == pytest.approx(want_res, rel=1e-3, abs=1e-6 * np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,M,J", [(64, 2048, 4), (256, 65536, 6)])
+def test_tile_schedules_agree(n, M, J, tmp_path):
+    """Every tile side gives the same Phi / Phi^H (the schedule is not the method),
+    and the autotuner picks one of them and caches it."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import autotune, binding
+
+    rng = np.random.default_rng(n + 5)
+    uv = inputs.uv_variable_density(M, n, rng).astype(np.float32).astype(np.float64)
+    x = inputs.random_image(n, rng)
+    v = inputs.random_vis(M, rng)
+    want_y = me.phi(x, uv, J)
+    want_x = me.phi_adj(v, uv, n, J)
+    for t in autotune.valid_tiles(n, J):
+        ctx = binding.Context(n, uv.astype(np.float32), J=J, tile=t)
+        assert rel_err(host(ctx.phi(dev(x, torch))), want_y) <= TOL
+        assert rel_err(host(ctx.phi_adj(dev(v, torch))), want_x) <= TOL
+    cache = str(tmp_path / "tune.json")
+    entry = autotune.autotune_tile(n, uv, J, cache_path=cache, reps=3)
+    assert entry["tile"] in autotune.valid_tiles(n, J)
+    assert autotune.autotune_tile(n, uv, J, cache_path=cache)["tile"] == entry["tile"]
