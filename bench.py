@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sdmm256", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="sdmm256", choices=sorted(inputs.WORKLOADS) + ["batch32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     return ap.parse_args()
@@ -358,8 +358,65 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """32 uneven problems advanced together (one CUDA graph per batch iteration)
+    against the same problems stepped one after another."""
+    import torch
+
+    from paper_1307_4370_gb300 import binding
+
+    torch.cuda.set_device(0)
+    ws = inputs.batch_workloads(32)
+    states = []
+    for w in ws:
+        p = inputs.make_problem(w)
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+        y0 = ctx.phi(torch.tensor(p.x_true.astype(np.complex64), device="cuda"))
+        sig = float(torch.linalg.vector_norm(y0).item()) / math.sqrt(w.M) * 10 ** (-w.isnr_db / 20)
+        y = y0 + sig * torch.tensor(p.noise_unit.astype(np.complex64), device="cuda")
+        st = ctx.sdmm_state()
+        st.init(y, binding.l2_bound(w.M, sig), cg_iters=w.cg_iters)
+        states.append(st)
+    batch = binding.Batch(states)
+    batch.step(max(3, args.warmup))
+    for st in states:
+        st.step()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    l0 = binding.launch_count()
+    a.record(stream)
+    batch.step(K)
+    b.record(stream)
+    torch.cuda.synchronize()
+    launches = binding.launch_count() - l0
+    batched_ms = a.elapsed_time(b)
+    a.record(stream)
+    for _ in range(K):
+        for st in states:
+            st.step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    total_iters = K * len(ws)
+    out = {"metric": "SDMM-SARA instance-iterations/sec (32 uneven problems)", "value": total_iters / (batched_ms / 1e3),
+           "unit": "instance-iterations/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup),
+           "ms_per_step": batched_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch32: 32 problems, n in {128,192,256,384,512}, M in [0.2N, 2N], J in {4,6}",
+                      "sizes": [[w.n, w.M, w.J] for w in ws], "l2": "not flushed (one graph per batch iteration)"},
+           "sequential": {"value": total_iters / (seq_ms / 1e3), "unit": "instance-iterations/s",
+                          "note": "same problems, one CUDA-graph step per problem in turn"},
+           "gpu_launches": launches}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "batch32":
+        run_batch(args)
+        return
     w = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)

@@ -287,6 +287,26 @@ int purify_sdmm_export(purify_ctx* ctx, purify_sdmm_state* st, void* host_buf,
 int purify_sdmm_import(purify_ctx* ctx, purify_sdmm_state* st, const void* host_buf,
                        size_t bytes, purify_stream_t stream);
 
+/* Batched SDMM: `count` independent problems (eq. delta), each with its own
+ * context and state and of any sizes, advanced together.  §4.5 discusses
+ * parallel evaluation of SDMM's independent parts; here whole problems run
+ * side by side.  One batch iteration is one CUDA graph with one branch per
+ * problem (captured at the first step, recaptured when a problem's cg_iters
+ * or data format changes), so the kernels of the problems overlap on the GPU.
+ * Contexts and states must be distinct, on one device, and already
+ * initialised (purify_sdmm_init).  purify_batch_step runs `iters` iterations
+ * of every problem on `stream`; each state can be read as usual afterwards.
+ * The batch does not own the contexts or states. */
+typedef struct purify_batch purify_batch;
+int purify_batch_create(purify_batch** out, purify_ctx* const* ctxs,
+                        purify_sdmm_state* const* states, int32_t count);
+int purify_batch_step(purify_batch* batch, int32_t iters, purify_stream_t stream);
+/* Number of problems and of kernels in one batch iteration (0 before the
+ * first step). */
+int purify_batch_size(const purify_batch* batch, int32_t* count,
+                      int32_t* kernels_per_iteration);
+void purify_batch_destroy(purify_batch* batch);
+
 /* Kernel timing (measurement utility; the paper has no counterpart).
  * purify_profile_enable(ctx, 1) makes every later kernel launch of this
  * context record a CUDA event before and after it on its stream;

@@ -93,6 +93,10 @@ _SIGS = {
     "purify_profile_collect": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(_i32)]),
     "purify_launch_count": (ctypes.c_uint64, []),
+    "purify_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32]),
+    "purify_batch_step": (ctypes.c_int, [_vp, _i32, _vp]),
+    "purify_batch_size": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "purify_batch_destroy": (None, [_vp]),
 }
 
 
@@ -414,3 +418,36 @@ class SdmmState:
 def l2_bound(M: int, sigma: float) -> float:
     """eps = sqrt((2M + 4 sqrt M) sigma^2 / 2), the chi^2 bound of §6."""
     return math.sqrt((2.0 * M + 4.0 * math.sqrt(M)) * sigma * sigma / 2.0)
+
+
+class Batch:
+    """Independent SDMM problems advanced together (one CUDA graph per iteration)."""
+
+    def __init__(self, states: list[SdmmState]):
+        self.lib = load()
+        self.states = list(states)  # keep the contexts and states alive
+        n = len(self.states)
+        ctxs = (_vp * n)(*[st.c.ctx for st in self.states])
+        sts = (_vp * n)(*[st.st for st in self.states])
+        out = _vp()
+        _check("purify_batch_create", self.lib.purify_batch_create(ctypes.byref(out), ctxs, sts, n))
+        self.b = out.value
+
+    def step(self, iters: int = 1, stream=None) -> None:
+        _check("purify_batch_step", self.lib.purify_batch_step(self.b, int(iters), _stream(stream)))
+
+    def kernels_per_iteration(self) -> int:
+        cnt, k = _i32(), _i32()
+        _check("purify_batch_size", self.lib.purify_batch_size(self.b, ctypes.byref(cnt), ctypes.byref(k)))
+        return int(k.value)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.lib.purify_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

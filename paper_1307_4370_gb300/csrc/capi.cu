@@ -392,8 +392,12 @@ int load_data(purify_ctx* c, purify_sdmm_state* st, const float* y, cudaStream_t
   return PURIFY_OK;
 }
 
+}  // namespace
+
+namespace purify {
+
 // Algorithm 1 steps 5-9 for one iteration, enqueued on s.
-int enqueue_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
+int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
   // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r holds r0 = b - Q x_hat(t-1))
   const int k = st->params.cg_iters;
@@ -432,6 +436,10 @@ int enqueue_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   st->launches_per_step = (int)(g_launches.load(std::memory_order_relaxed) - l0);
   return PURIFY_OK;
 }
+
+}  // namespace purify
+
+namespace {
 
 int drop_graph(purify_sdmm_state* st) {
   if (st->step_exec) {
@@ -778,14 +786,14 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (!st->params.use_graph || c->prof.on) {
-    TRY(enqueue_step(c, st, s));
+    TRY(enqueue_sdmm_step(c, st, s));
   } else {
     const int key = st->params.cg_iters * 2 + st->y_bf16;
     if (!st->step_exec || st->graph_cg_iters != key) {
       TRY(drop_graph(st));
       if (!st->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
       TRY_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeRelaxed));
-      const int rc = enqueue_step(c, st, st->cap_stream);
+      const int rc = enqueue_sdmm_step(c, st, st->cap_stream);
       cudaGraph_t graph = nullptr;
       const cudaError_t e = cudaStreamEndCapture(st->cap_stream, &graph);
       if (rc != PURIFY_OK || e != cudaSuccess) {
@@ -800,6 +808,7 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
         return PURIFY_E_CUDA;
       }
       st->graph_cg_iters = key;
+      g_launches.fetch_sub((unsigned long long)st->launches_per_step, std::memory_order_relaxed);  // capture only
     }
     TRY_CUDA(cudaGraphLaunch(st->step_exec, s));
     g_launches.fetch_add(st->launches_per_step, std::memory_order_relaxed);

@@ -316,6 +316,7 @@ namespace purify {
 
 // Launchers (implemented in the .cu files).
 int check_cuda(cudaError_t e);
+int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s);  // capi.cu
 
 // nufft.cu
 // kRowInCgUpd: apply the pending CG vector update, then transform r;

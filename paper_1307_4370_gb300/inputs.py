@@ -218,3 +218,19 @@ def uniform_uv(M: int, rng: np.random.Generator) -> np.ndarray:
     uv = rng.uniform(-np.pi, np.pi, size=(M, 2)).astype(np.float32)
     uv = np.where(uv >= np.float32(np.pi), np.nextafter(np.float32(np.pi), np.float32(0)), uv)
     return uv.astype(np.float64)
+
+
+def batch_workloads(count: int = 32, seed: int = SEED_BASE + 3) -> list[Workload]:
+    """Uneven independent problems: image side uniform in {128, 192, 256, 384,
+    512}, M uniform in [0.2 N, 2 N], Kaiser-Bessel support 4 or 6, 200
+    iterations each (each problem draws its own image and coverage)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.choice([128, 192, 256, 384, 512]))
+        N = n * n
+        M = int(rng.integers(int(0.2 * N), 2 * N + 1))
+        J = int(rng.choice([4, 6]))
+        out.append(Workload(f"batch{k}", n=n, M=M, J=J, n_src=max(20, n // 2), diffuse=True,
+                            T=200, rounds=1, seed=seed * 100 + k))
+    return out
