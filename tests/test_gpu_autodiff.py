@@ -4,8 +4,11 @@
   gradient of Re <v, Phi x> with respect to x is Phi^H v (oracle).
 * Directional derivatives of ||x_K - x_true||^2 with respect to the
   per-visibility weights w and the SARA weights omega, from the checkpointed
-  reverse pass on the GPU, match central finite differences (h = 1e-3) of the
-  FP64 oracle's K-iteration SDMM to 1e-3 relative.
+  reverse pass on the GPU, match central finite differences of the FP64
+  oracle's K-iteration SDMM to 1e-3 relative.  The map is only piecewise
+  smooth (soft threshold, ball projection): on this problem central
+  differences with h = 1e-3 themselves move by ~1e-3 relative from their
+  h -> 0 limit (measured with the oracle), so the differences use h = 1e-4.
 * On the 256 x 256, M = 65536, K = 20 problem the checkpointed gradient equals
   the one-segment gradient and needs less memory.
 """
@@ -81,7 +84,7 @@ def test_sdmm_gradients_against_oracle_finite_differences():
     go = ot.grad.double().cpu().numpy()
     L0 = oracle_loss(p, y, eps, wv0, om0, gamma, K, cg_iters)
     assert float(loss.item()) == pytest.approx(L0, rel=1e-3)
-    h = 1e-3
+    h = 1e-4
     for k in range(2):
         dw = rng.standard_normal(w.M)
         fd = (oracle_loss(p, y, eps, wv0 + h * dw, om0, gamma, K, cg_iters)
