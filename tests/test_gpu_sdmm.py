@@ -179,3 +179,38 @@ def test_profiler_and_launch_counter():
             "idwt_level", "sdmm_l2"} <= names
     assert sum(r[1] for r in prof) == per_step
     assert all(r[2] > 0 for r in prof)
+
+
+def test_mixed_precision_full_size_errors(capsys):
+    """1024 x 1024, M = 2^21 with radial arcs: two SDMM iterations (2 CG steps)
+    with complex64 data and with bf16-stored data, each against the FP64 oracle;
+    the error of every output is printed (recorded in the design notes)."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p = inputs.make_problem("sdmm1024")
+    w = p.workload
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db)
+    y = y.astype(np.complex64).astype(np.complex128)
+    iters, cg_iters = 2, 2
+    ops = simulate.operators(p.uv, w.n, w.J)
+    ref = osdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=iters, cg_iters=cg_iters)
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    errs = {}
+    for mode in ("c64", "bf16"):
+        st = ctx.sdmm_state()
+        st.init(dev(y, torch), eps, cg_iters=cg_iters)
+        if mode == "bf16":
+            st.set_data_bf16(dev(y, torch))
+        for _ in range(iters):
+            st.step()
+        x = host(st.get_image())
+        rep = st.report()
+        errs[mode] = {"x_hat": rel_err(x, ref.x_hat),
+                      "nu": abs(rep["nu"] - ref.history[-1]["nu"]) / ref.history[-1]["nu"],
+                      "f1": abs(rep["f1"] - ref.history[-1]["f1"]) / ref.history[-1]["f1"]}
+    with capsys.disabled():
+        print("\nsdmm1024 errors vs FP64 oracle:", errs)
+    assert errs["c64"]["x_hat"] <= 1e-4
+    assert errs["bf16"]["x_hat"] <= 1e-2
+    assert errs["c64"]["nu"] <= 1e-4 and errs["c64"]["f1"] <= 1e-4
