@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--workload", default="sdmm256", choices=sorted(inputs.WORKLOADS) + ["batch32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
+    ap.add_argument("--precision", choices=["c64", "bf16"], default="c64",
+                    help="storage of the measured visibilities y (bf16 pairs with per-4096 scales)")
     return ap.parse_args()
 
 
@@ -228,6 +230,8 @@ def run_gpu(args, w):
     eps = binding.l2_bound(w.M, sig)
     st = ctx.sdmm_state()
     st.init(y, eps, cg_iters=w.cg_iters)
+    if args.precision == "bf16":
+        st.set_data_bf16(y)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     state = {"iters": 0, "round": 0}
@@ -294,7 +298,10 @@ def run_gpu(args, w):
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         flush.fill_(float(k))
-        st.set_data(y_host)      # H2D of this step's data
+        if args.precision == "bf16":
+            st.set_data_bf16(y_host)  # H2D of this step's data, stored as bf16 on the device
+        else:
+            st.set_data(y_host)       # H2D of this step's data
         one_step()
         st.get_image(x_host)     # D2H of the step's result (synchronises)
     barrier()
@@ -338,7 +345,8 @@ def run_gpu(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**workload_config(w), "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "config": {**workload_config(w), "y_storage": args.precision,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "cuda_graph": True, "tile": tune["tile"], "tile_ms": tune["timings"],
                        "parallelism": f"{world} independent problems (one per GPU)"},
             "phi_phiadj": {"value": gvis, "unit": "Gvis/s", "ms": phi_ms},
