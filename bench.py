@@ -198,6 +198,23 @@ def peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def rank_workload(w: inputs.Workload, rank: int) -> inputs.Workload:
+    """The independent problem a rank solves: same shape, its own seed."""
+    return inputs.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})
+
+
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks (the timing rule: the slowest rank counts)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -217,8 +234,7 @@ def run_gpu(args, w):
         cpu_entry = cpu_baseline_entry(w, args.cpu_seconds)
 
     # each rank: its own independent problem of the same shape
-    wr = inputs.Workload(**{**w.__dict__, "seed": w.seed + 1000 * rank})
-    p = inputs.make_problem(wr)
+    p = inputs.make_problem(rank_workload(w, rank))
     from paper_1307_4370_gb300 import autotune
     tune = autotune.autotune_tile(w.n, p.uv, w.J, reps=10)  # grid-tile schedule, measured and cached
     ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J, tile=tune["tile"])
@@ -267,11 +283,7 @@ def run_gpu(args, w):
     barrier()
     gpu_launches = binding.launch_count() - l0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), dev)
     value = world * args.steps / (total_ms / 1e3)
 
     # --- Phi + Phi^H visibility rate (public calls, L2 flushed) ----------
@@ -305,11 +317,7 @@ def run_gpu(args, w):
         one_step()
         st.get_image(x_host)     # D2H of the step's result (synchronises)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     # the flush is inside this wall-clock region: take it out with its own timing
     fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
     for a, b in fl:

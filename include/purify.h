@@ -84,7 +84,7 @@ typedef enum {
 
 /* Problem description (§3.1 eq. ri4, §5 eq. opmodel, §3.3).
  *   n           image side; N = n*n; a multiple of 2^levels; 2n must factor
- *               as 2^a 3^b with b <= 1; 8 <= n <= 4096.
+ *               as 2^a 3^b with b <= 1; 8 <= n <= 2048.
  *   M           number of visibilities, 1 <= M <= 2^31 - 1.
  *   J           Kaiser-Bessel support per axis: 2, 4, 6 or 8.
  *   oversample  must be 2 (§6 uses k = 2; the grid is 2n x 2n).

@@ -1,0 +1,52 @@
+"""The multi-rank host logic of bench.py on two gloo ranks (no GPU).
+
+Under torchrun every rank solves its own problem (weak scaling, no collective
+on the data path); the ranks only agree on the slowest time.  The reference
+arm runs on rank 0 alone.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    slowest = bench.max_over_ranks(1.5 + rank, "cpu")
+    w = bench.rank_workload(bench.inputs.WORKLOADS["sdmm64"], rank)
+    out[rank] = (slowest, w.seed)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_agree_on_the_slowest_time_and_draw_independent_problems():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 2.5
+    assert res[0][1] != res[1][1]
+
+
+def test_reference_arm_prints_on_rank_zero_only(capsys, monkeypatch):
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    ns = type("Args", (), {"steps": 1, "warmup": 0, "gpus": 2})()
+    bench.run_reference(ns, bench.inputs.WORKLOADS["sdmm64"])
+    assert capsys.readouterr().out == ""
