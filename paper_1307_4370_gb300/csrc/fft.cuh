@@ -151,4 +151,145 @@ __device__ __forceinline__ void fft_smem(float2* buf, SigLayout lay, const FftPl
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused driver: the first stage (Ns = 1) reads its inputs from global memory
+// and the last stage (Ns = L / R) hands its outputs to global memory, so a
+// transform costs one shared-memory pass less on each side.  Every thread
+// issues all of its global loads (inputs and twiddles) before it uses any of
+// them.
+//
+//   Src: typename Raw; Raw fetch(s, e) const;  float2 prep(const Raw&, s, e) const
+//   Dst: typename Aux; Aux fetch(s, e) const;  void put(s, e, float2, const Aux&)
+// (s = signal, e = element; Dst::fetch runs before the last stage's arithmetic
+// so the epilogue operands are in flight meanwhile.)
+// ---------------------------------------------------------------------------
+template <int R, int EPT, bool SIG_FAST, class Src>
+__device__ __forceinline__ void stage_first(float2* buf, SigLayout lay, const Div& lr, const Div& dsig, int nsig,
+                                            const Src& src, float2* tws, const float2 (&twr)[EPT], int L) {
+  constexpr int NB = EPT / R;
+  const int LR = lr.d;
+  const int nbfly = nsig * LR;
+  typename Src::Raw raw[EPT];
+  int ss[NB], jj[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * blockDim.x;
+    int s = 0, j = 0;
+    if (b < nbfly) {
+      if (SIG_FAST) { j = udiv(b, dsig); s = b - j * nsig; }
+      else { s = udiv(b, lr); j = b - s * LR; }
+#pragma unroll
+      for (int r = 0; r < R; ++r) raw[k * R + r] = src.fetch(s, j + r * LR);
+    }
+    ss[k] = s;
+    jj[k] = j;
+  }
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < L) tws[i] = twr[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * blockDim.x;
+    if (b < nbfly) {
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = src.prep(raw[k * R + r], ss[k], jj[k] + r * LR);
+      dft_small<R>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[lay.at(ss[k], jj[k] * R + r)] = v[r];
+    }
+  }
+}
+
+template <int R, int EPT, bool SIG_FAST, class Dst>
+__device__ __forceinline__ void stage_last(const float2* buf, SigLayout lay, const Div& lr, const Div& dsig, int nsig,
+                                           const float2* tw, Dst& dst) {
+  constexpr int NB = EPT / R;
+  const int LR = lr.d;
+  const int nbfly = nsig * LR;
+  typename Dst::Aux aux[EPT];
+  int ss[NB], jj[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * blockDim.x;
+    int s = 0, j = 0;
+    if (b < nbfly) {
+      if (SIG_FAST) { j = udiv(b, dsig); s = b - j * nsig; }
+      else { s = udiv(b, lr); j = b - s * LR; }
+#pragma unroll
+      for (int r = 0; r < R; ++r) aux[k * R + r] = dst.fetch(s, j + r * LR);
+    }
+    ss[k] = s;
+    jj[k] = j;
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int b = threadIdx.x + k * blockDim.x;
+    if (b < nbfly) {
+      const int j = jj[k];
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = buf[lay.at(ss[k], j + r * LR)];
+      // last stage: Ns = L / R, so k = j and the twiddle step is 1
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * j]);
+      dft_small<R>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst.put(ss[k], j + r * LR, v[r], aux[k * R + r]);
+    }
+  }
+}
+
+// Forward FFT of nsig signals of length L (at least two stages): inputs from
+// `src`, outputs to `dst`, `buf` holds the signals in between and `tws` gets
+// the L twiddles exp(-2 pi i t / L) copied from `tw`.
+template <int EPT, bool SIG_FAST, class Src, class Dst>
+__device__ __forceinline__ void fft_fused(float2* buf, SigLayout lay, const FftPlan& plan, int nsig, float2* tws,
+                                          const float2* __restrict__ tw, const Src& src, Dst& dst) {
+  const Div dsig = make_div(nsig);
+  const int L = plan.L;
+  float2 twr[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < L) twr[k] = __ldg(&tw[i]);
+  }
+  {
+    const int R = plan.radix[0];
+    const Div& lr = plan.lr[0];
+    if constexpr (EPT % 8 == 0) { if (R == 8) stage_first<8, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, src, tws, twr, L); }
+    if constexpr (EPT % 4 == 0) { if (R == 4) stage_first<4, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, src, tws, twr, L); }
+    if constexpr (EPT % 3 == 0) { if (R == 3) stage_first<3, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, src, tws, twr, L); }
+    if constexpr (EPT % 2 == 0) { if (R == 2) stage_first<2, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, src, tws, twr, L); }
+  }
+  __syncthreads();
+  for (int st = 1; st < plan.nst - 1; ++st) {
+    const int R = plan.radix[st];
+    const Div& ns = plan.ns[st];
+    const Div& lr = plan.lr[st];
+    if constexpr (EPT % 8 == 0) {
+      if (R == 8) { stockham_stage<8, EPT, SIG_FAST>(buf, lay, L, ns, lr, dsig, nsig, tws); continue; }
+    }
+    if constexpr (EPT % 4 == 0) {
+      if (R == 4) { stockham_stage<4, EPT, SIG_FAST>(buf, lay, L, ns, lr, dsig, nsig, tws); continue; }
+    }
+    if constexpr (EPT % 3 == 0) {
+      if (R == 3) { stockham_stage<3, EPT, SIG_FAST>(buf, lay, L, ns, lr, dsig, nsig, tws); continue; }
+    }
+    if constexpr (EPT % 2 == 0) {
+      if (R == 2) { stockham_stage<2, EPT, SIG_FAST>(buf, lay, L, ns, lr, dsig, nsig, tws); continue; }
+    }
+  }
+  {
+    const int R = plan.radix[plan.nst - 1];
+    const Div& lr = plan.lr[plan.nst - 1];
+    if constexpr (EPT % 8 == 0) { if (R == 8) stage_last<8, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, tws, dst); }
+    if constexpr (EPT % 4 == 0) { if (R == 4) stage_last<4, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, tws, dst); }
+    if constexpr (EPT % 3 == 0) { if (R == 3) stage_last<3, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, tws, dst); }
+    if constexpr (EPT % 2 == 0) { if (R == 2) stage_last<2, EPT, SIG_FAST>(buf, lay, lr, dsig, nsig, tws, dst); }
+  }
+}
+
 }  // namespace purify

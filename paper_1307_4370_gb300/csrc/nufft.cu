@@ -10,6 +10,8 @@
 //           k_col_inv   inverse column DFTs, keeping the n rows of the image;
 //           k_row_inv   inverse row DFTs, crop Z^T and D, with fused epilogues
 //                       for the CG operator Q = Phi^H Phi + 2I and the SDMM step.
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "reduce.cuh"
@@ -27,10 +29,12 @@ struct FftShape {
 
 static int pick_ept(int L) { return (L % 3 == 0) ? 12 : 8; }
 
-// Row passes: nsig rows per CTA, about 256 threads, nsig divides n.
+// Row passes: nsig rows per CTA, at most 256 threads (16 elements per thread
+// for L = 4096), nsig divides n.
 static FftShape row_shape(const purify_ctx* c) {
   FftShape f;
   f.ept = pick_ept(c->L);
+  if (f.ept == 8 && c->L / 8 > 256) f.ept = 16;
   int nsig = 1;
   while (nsig * 2 * c->L / f.ept <= 128 && c->n % (nsig * 2) == 0) nsig *= 2;
   f.nsig = nsig;
@@ -63,92 +67,136 @@ static void allow_smem(K kernel, size_t bytes) {
 // (single-reduction CG: p = r + beta p, s = w + beta s, x += alpha p,
 // r -= alpha s), and v is the new r (kRowInCgUpd) or x (kRowInCgFinish).
 // ---------------------------------------------------------------------------
-template <int EPT, int MODE>
-__global__ void __launch_bounds__(1024) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
-                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
-                          const DevScalars* __restrict__ sc) {
-  extern __shared__ float2 sm[];
-  const int L = plan.L;
-  const Div dsig = make_div(nsig), dn = make_div(n);
-  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
-  const int r0 = blockIdx.x * nsig;
-  const float invL = 1.0f / (float)L;
-  float alpha = 0.f, beta = 0.f;
-  bool first = false;
-  if (MODE != kRowInPlain) {
-    alpha = (float)sc->alpha;
-    beta = (float)sc->beta;
-    first = sc->upd_first != 0;
-  }
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = udiv(idx, plan.divL), e = idx - s * L;
-    const int r = r0 + s;
+struct EmptyAux {};
+
+struct RawPlain {
+  float2 v;
+  float f;
+  int off;  // pixel index, or -1 in the zero padding
+};
+struct RawCg {
+  float2 r, w, p, s, x;
+  float f;
+  int off;
+};
+
+template <int MODE>
+struct RowFwdSrc {
+  using Raw = typename std::conditional<MODE == kRowInPlain, RawPlain, RawCg>::type;
+  RowInArgs a;
+  const float* dz;
+  int n, L, r0;
+  float invL, alpha, beta;
+  bool first;
+  __device__ __forceinline__ Raw fetch(int s, int e) const {
+    Raw o;
+    const int row = r0 + s;
     int cc = e + (n >> 1);
     if (cc >= L) cc -= L;
-    float2 v = make_float2(0.f, 0.f);
+    o.off = -1;
     if (cc < n) {
-      const size_t off = (size_t)r * n + cc;
-      if (MODE == kRowInPlain) {
-        v = a.in[off];
+      o.off = row * n + cc;
+      o.f = __ldg(&dz[row]) * __ldg(&dz[cc]) * invL;
+      if constexpr (MODE == kRowInPlain) {
+        o.v = a.in[o.off];
       } else {
-        const float2 rr = a.r[off], ww = a.w[off];
-        float2 pp, ss;
-        if (first) {
-          pp = rr;
-          ss = ww;
-        } else {
-          const float2 po = a.p[off], so = a.s[off];
-          pp = make_float2(fmaf(beta, po.x, rr.x), fmaf(beta, po.y, rr.y));
-          ss = make_float2(fmaf(beta, so.x, ww.x), fmaf(beta, so.y, ww.y));
+        o.r = a.r[o.off];
+        o.w = a.w[o.off];
+        if (!first) {
+          o.p = a.p[o.off];
+          o.s = a.s[o.off];
         }
-        float2 xx = a.x[off];
-        xx = make_float2(fmaf(alpha, pp.x, xx.x), fmaf(alpha, pp.y, xx.y));
-        const float2 rn = make_float2(fmaf(-alpha, ss.x, rr.x), fmaf(-alpha, ss.y, rr.y));
-        a.p[off] = pp;
-        a.s[off] = ss;
-        a.x[off] = xx;
-        a.r[off] = rn;
-        v = (MODE == kRowInCgUpd) ? rn : xx;
+        o.x = a.x[o.off];
       }
-      const float f = dz[r] * dz[cc] * invL;
-      v = cscale(v, f);
     }
-    sm[s * L + e] = v;
+    return o;
   }
-  __syncthreads();
-  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = udiv(idx, plan.divL), e = idx - s * L;
-    half[(size_t)(r0 + s) * L + e] = sm[s * L + e];
+  __device__ __forceinline__ float2 prep(const Raw& o, int, int) const {
+    if (o.off < 0) return make_float2(0.f, 0.f);
+    if constexpr (MODE == kRowInPlain) {
+      return cscale(o.v, o.f);
+    } else {
+      float2 pp = o.r, ss = o.w;
+      if (!first) {
+        pp = make_float2(fmaf(beta, o.p.x, o.r.x), fmaf(beta, o.p.y, o.r.y));
+        ss = make_float2(fmaf(beta, o.s.x, o.w.x), fmaf(beta, o.s.y, o.w.y));
+      }
+      const float2 xx = make_float2(fmaf(alpha, pp.x, o.x.x), fmaf(alpha, pp.y, o.x.y));
+      const float2 rn = make_float2(fmaf(-alpha, ss.x, o.r.x), fmaf(-alpha, ss.y, o.r.y));
+      a.p[o.off] = pp;
+      a.s[o.off] = ss;
+      a.x[o.off] = xx;
+      a.r[o.off] = rn;
+      return cscale(MODE == kRowInCgUpd ? rn : xx, o.f);
+    }
   }
+};
+
+struct RowStoreDst {  // row-major rows of length L
+  using Aux = EmptyAux;
+  float2* out;
+  int L;
+  __device__ __forceinline__ Aux fetch(int, int) const { return Aux{}; }
+  __device__ __forceinline__ void put(int s, int e, float2 v, const Aux&) { out[(size_t)s * L + e] = v; }
+};
+
+template <int EPT, int MODE>
+__global__ void __launch_bounds__(256) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
+                                                 const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
+                                                 const DevScalars* __restrict__ sc) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  RowFwdSrc<MODE> src;
+  src.a = a;
+  src.dz = dz;
+  src.n = n;
+  src.L = L;
+  src.r0 = blockIdx.x * nsig;
+  src.invL = 1.0f / (float)L;
+  src.alpha = src.beta = 0.f;
+  src.first = false;
+  if (MODE != kRowInPlain) {
+    src.alpha = (float)sc->alpha;
+    src.beta = (float)sc->beta;
+    src.first = sc->upd_first != 0;
+  }
+  RowStoreDst dst{half + (size_t)src.r0 * L, L};
+  fft_fused<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, sm + nsig * L, tw, src, dst);
 }
 
 // ---------------------------------------------------------------------------
 // Forward column pass: column c of the grid holds half[r][c] at row
 // (r - n/2) mod L and zeros elsewhere; DFT along the column into X.
 // ---------------------------------------------------------------------------
-template <int EPT>
-__global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ half, float2* __restrict__ X,
-                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
-  extern __shared__ float2 sm[];
-  const int L = plan.L;
-  const Div dsig = make_div(nsig), dn = make_div(n);
-  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
-  const int c0 = blockIdx.x * nsig;
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = udiv(idx, dsig), s = idx - e * nsig;
+struct ColFwdSrc {
+  using Raw = float2;
+  const float2* half;
+  int n, L, c0;
+  __device__ __forceinline__ Raw fetch(int s, int e) const {
     int r = e + (n >> 1);
     if (r >= L) r -= L;
-    sm[e * nsig + s] = (r < n) ? half[(size_t)r * L + c0 + s] : make_float2(0.f, 0.f);
+    return r < n ? half[(size_t)r * L + c0 + s] : make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = udiv(idx, dsig), s = idx - e * nsig;
-    X[(size_t)e * L + c0 + s] = sm[e * nsig + s];
-  }
+  __device__ __forceinline__ float2 prep(const Raw& v, int, int) const { return v; }
+};
+
+struct ColStoreDst {  // column c0 + s of an L x L grid
+  using Aux = EmptyAux;
+  float2* X;
+  int L, c0;
+  __device__ __forceinline__ Aux fetch(int, int) const { return Aux{}; }
+  __device__ __forceinline__ void put(int s, int e, float2 v, const Aux&) { X[(size_t)e * L + c0 + s] = v; }
+};
+
+template <int EPT>
+__global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ half, float2* __restrict__ X,
+                                                  const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int c0 = blockIdx.x * nsig;
+  ColFwdSrc src{half, n, L, c0};
+  ColStoreDst dst{X, L, c0};
+  fft_fused<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, sm + nsig * L, tw, src, dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,29 +463,38 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
 }
 
 // ---------------------------------------------------------------------------
-// Inverse column pass: inverse DFT of columns of X, keep rows (r - n/2) mod L.
+// Inverse column pass: inverse DFT of columns of X (by conjugation), keep rows
+// (r - n/2) mod L.
 // ---------------------------------------------------------------------------
+struct ColInvSrc {
+  using Raw = float2;
+  const float2* X;
+  int L, c0;
+  __device__ __forceinline__ Raw fetch(int s, int e) const { return X[(size_t)e * L + c0 + s]; }
+  __device__ __forceinline__ float2 prep(const Raw& v, int, int) const { return cconj(v); }
+};
+
+struct ColCropDst {
+  using Aux = EmptyAux;
+  float2* half;
+  int n, L, c0;
+  __device__ __forceinline__ Aux fetch(int, int) const { return Aux{}; }
+  __device__ __forceinline__ void put(int s, int e, float2 v, const Aux&) {
+    int r = e + (n >> 1);
+    if (r >= L) r -= L;
+    if (r < n) half[(size_t)r * L + c0 + s] = cconj(v);
+  }
+};
+
 template <int EPT>
 __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, float2* __restrict__ half,
-                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
+                                                  const float2* __restrict__ tw, FftPlan plan, int n, int nsig) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
-  const Div dsig = make_div(nsig), dn = make_div(n);
-  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
   const int c0 = blockIdx.x * nsig;
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int e = udiv(idx, dsig), s = idx - e * nsig;
-    sm[e * nsig + s] = cconj(X[(size_t)e * L + c0 + s]);
-  }
-  __syncthreads();
-  fft_smem<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, tws);
-  for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
-    const int r = udiv(idx, dsig), s = idx - r * nsig;
-    int e = r - (n >> 1);
-    if (e < 0) e += L;
-    half[(size_t)r * L + c0 + s] = cconj(sm[e * nsig + s]);
-  }
+  ColInvSrc src{X, L, c0};
+  ColCropDst dst{half, n, L, c0};
+  fft_fused<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, sm + nsig * L, tw, src, dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -450,59 +507,91 @@ __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, 
 //   SDMM:  positivity branch (z3, u3) and the warm-start CG residual
 //          r0 = x1 + u3 - 2 x_hat + Phi^H v
 // ---------------------------------------------------------------------------
-template <int EPT, int MODE>
-__global__ void __launch_bounds__(1024) k_row_inv(const float2* __restrict__ half, RowOutArgs a, const float* __restrict__ dz,
-                          const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
-                          double* partials, DevScalars* sc) {
-  extern __shared__ float2 sm[];
-  const int L = plan.L;
-  const Div dsig = make_div(nsig), dn = make_div(n);
-  float2* tws = sm + nsig * L;  // twiddles staged next to the signals
-  for (int i = threadIdx.x; i < L; i += blockDim.x) tws[i] = __ldg(&tw[i]);
-  const int r0 = blockIdx.x * nsig;
-  for (int idx = threadIdx.x; idx < nsig * L; idx += blockDim.x) {
-    const int s = udiv(idx, plan.divL), e = idx - s * L;
-    sm[s * L + e] = cconj(half[(size_t)(r0 + s) * L + e]);
-  }
-  __syncthreads();
-  fft_smem<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, tws);
-  const float invL = 1.0f / (float)L;
+struct RowInvSrc {
+  using Raw = float2;
+  const float2* half;
+  int L, r0;
+  __device__ __forceinline__ Raw fetch(int s, int e) const { return half[(size_t)(r0 + s) * L + e]; }
+  __device__ __forceinline__ float2 prep(const Raw& v, int, int) const { return cconj(v); }
+};
+
+struct AuxPix {
+  float2 p, z3, x1;
+  float f;
+  int off;  // pixel index, or -1 outside the crop
+};
+
+template <int MODE>
+struct RowInvDst {
+  using Aux = AuxPix;
+  RowOutArgs a;
+  const float* dz;
+  int n, L, r0;
+  float invL;
   FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
-  for (int idx = threadIdx.x; idx < nsig * n; idx += blockDim.x) {
-    const int s = udiv(idx, dn), c = idx - s * n;
-    const int r = r0 + s;
-    int e = c - (n >> 1);
-    if (e < 0) e += L;
-    const float f = dz[r] * dz[c] * invL;
-    const float2 v = cscale(cconj(sm[s * L + e]), f);
-    const size_t off = (size_t)r * n + c;
+  __device__ __forceinline__ Aux fetch(int s, int e) const {
+    Aux o;
+    const int row = r0 + s;
+    int c = e + (n >> 1);
+    if (c >= L) c -= L;
+    o.off = -1;
+    if (c < n) {
+      o.off = row * n + c;
+      o.f = __ldg(&dz[row]) * __ldg(&dz[c]) * invL;
+      if (MODE != kRowOutPlain) o.p = a.p[o.off];
+      if (MODE == kRowOutSdmm) {
+        o.z3 = a.z3[o.off];
+        o.x1 = a.x1[o.off];
+      }
+    }
+    return o;
+  }
+  __device__ __forceinline__ void put(int, int, float2 w, const Aux& o) {
+    if (o.off < 0) return;
+    const float2 v = cscale(cconj(w), o.f);
     if (MODE == kRowOutPlain) {
-      a.out[off] = v;
+      a.out[o.off] = v;
     } else if (MODE == kRowOutCgQ) {
-      const float2 p = a.p[off];
+      const float2 p = o.p;
       const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
-      a.out[off] = q;
+      a.out[o.off] = q;
       part[0].add_prod(p.x, p.x);  // <r, r>
       part[0].add_prod(p.y, p.y);
       part[1].add_prod(p.x, q.x);  // Re <w, r>
       part[1].add_prod(p.y, q.y);
     } else {
-      const float2 xh = a.p[off];
-      const float2 z3 = a.z3[off];
-      const float2 a3 = cadd(xh, z3);
+      const float2 xh = o.p;
+      const float2 a3 = cadd(xh, o.z3);
       const float r3 = fmaxf(a3.x, 0.f);
       const float2 z3n = make_float2(a3.x - r3, a3.y);  // a3 - r3
       const float2 u3 = make_float2(r3 - z3n.x, -z3n.y);
-      const float2 x1 = a.x1[off];
       float2 r0v;
-      r0v.x = x1.x + u3.x - 2.f * xh.x + v.x;
-      r0v.y = x1.y + u3.y - 2.f * xh.y + v.y;
-      a.z3[off] = z3n;
-      a.out[off] = r0v;
+      r0v.x = o.x1.x + u3.x - 2.f * xh.x + v.x;
+      r0v.y = o.x1.y + u3.y - 2.f * xh.y + v.y;
+      a.z3[o.off] = z3n;
+      a.out[o.off] = r0v;
     }
   }
+};
+
+template <int EPT, int MODE>
+__global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half, RowOutArgs a,
+                                                 const float* __restrict__ dz, const float2* __restrict__ tw,
+                                                 FftPlan plan, int n, int nsig, double* partials, DevScalars* sc) {
+  extern __shared__ float2 sm[];
+  const int L = plan.L;
+  const int r0 = blockIdx.x * nsig;
+  RowInvSrc src{half, L, r0};
+  RowInvDst<MODE> dst;
+  dst.a = a;
+  dst.dz = dz;
+  dst.n = n;
+  dst.L = L;
+  dst.r0 = r0;
+  dst.invL = 1.0f / (float)L;
+  fft_fused<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, sm + nsig * L, tw, src, dst);
   if (MODE == kRowOutCgQ) {
-    double acc[2] = {part[0].value(), part[1].value()};
+    double acc[2] = {dst.part[0].value(), dst.part[1].value()};
     double tot[2];
     if (reduce_last_block<2>(acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], tot)) {
       const double gamma = tot[0], delta = tot[1];
@@ -541,6 +630,10 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
     if (mode == kRowInPlain) ROWF(8, kRowInPlain);
     else if (mode == kRowInCgUpd) ROWF(8, kRowInCgUpd);
     else ROWF(8, kRowInCgFinish);
+  } else if (rs.ept == 16) {
+    if (mode == kRowInPlain) ROWF(16, kRowInPlain);
+    else if (mode == kRowInCgUpd) ROWF(16, kRowInCgUpd);
+    else ROWF(16, kRowInCgFinish);
   } else {
     if (mode == kRowInPlain) ROWF(12, kRowInPlain);
     else if (mode == kRowInCgUpd) ROWF(12, kRowInCgUpd);
@@ -648,6 +741,10 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
     if (mode == kRowOutPlain) ROWI(8, kRowOutPlain);
     else if (mode == kRowOutCgQ) ROWI(8, kRowOutCgQ);
     else ROWI(8, kRowOutSdmm);
+  } else if (rs.ept == 16) {
+    if (mode == kRowOutPlain) ROWI(16, kRowOutPlain);
+    else if (mode == kRowOutCgQ) ROWI(16, kRowOutCgQ);
+    else ROWI(16, kRowOutSdmm);
   } else {
     if (mode == kRowOutPlain) ROWI(12, kRowOutPlain);
     else if (mode == kRowOutCgQ) ROWI(12, kRowOutCgQ);
