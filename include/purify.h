@@ -120,6 +120,11 @@ void purify_destroy(purify_ctx* ctx);
 /* Name of a status code (static string). */
 const char* purify_status_string(int status);
 
+/* Description of the last CUDA runtime error that a call made on this host
+ * thread reported as PURIFY_E_CUDA ("no CUDA error" if none); a static
+ * string. */
+const char* purify_last_error(void);
+
 /* Sizes of a context: N = n*n, M, q = number of bases, D = q*N. */
 int purify_sizes(const purify_ctx* ctx, int64_t* N, int64_t* M, int32_t* q,
                  int64_t* D);

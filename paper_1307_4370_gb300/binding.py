@@ -19,6 +19,7 @@ from . import build as _build
 _LIB = None
 
 PURIFY_OK = 0
+PURIFY_E_CUDA = -5
 STATUS_NAMES = {
     0: "PURIFY_OK", -1: "PURIFY_E_INVALID_ARG", -2: "PURIFY_E_SIZE", -3: "PURIFY_E_NOT_DEVICE_PTR",
     -4: "PURIFY_E_ALLOC", -5: "PURIFY_E_CUDA", -6: "PURIFY_E_TIMEOUT", -7: "PURIFY_E_UNSUPPORTED",
@@ -32,6 +33,8 @@ class PurifyError(RuntimeError):
     def __init__(self, func: str, status: int):
         self.status = status
         msg = _LIB.purify_status_string(status).decode() if _LIB is not None else str(status)
+        if _LIB is not None and status == PURIFY_E_CUDA:
+            msg += ": " + _LIB.purify_last_error().decode()
         super().__init__(f"{func} failed: {STATUS_NAMES.get(status, status)} ({msg})")
 
 
@@ -62,6 +65,7 @@ _SIGS = {
     "purify_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Desc), _vp, _vp]),
     "purify_destroy": (None, [_vp]),
     "purify_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "purify_last_error": (ctypes.c_char_p, []),
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),

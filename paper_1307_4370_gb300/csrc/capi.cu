@@ -14,7 +14,15 @@ using namespace purify;
 
 namespace purify {
 
-int check_cuda(cudaError_t e) { return e == cudaSuccess ? PURIFY_OK : PURIFY_E_CUDA; }
+// The last CUDA error a library call of this thread turned into
+// PURIFY_E_CUDA (reported by purify_last_error).
+thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+
+int check_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PURIFY_OK;
+  t_last_cuda_error = e;
+  return PURIFY_E_CUDA;
+}
 
 std::atomic<unsigned long long> g_launches{0};
 
@@ -182,6 +190,22 @@ __global__ void k_footprint(const float2* __restrict__ uv, int64_t M, KappaScale
   }
 }
 
+// Per tile-list entry: the sorted index, the start-cell key and the kappa
+// fractions (same arithmetic as the kernels), so the gridding needs no
+// frequency gather and no integer wrap per call.
+__global__ void k_list_setup(const int2* __restrict__ lk, const float2* __restrict__ uv, KappaScale ks, int64_t n,
+                             int4* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int2 v = lk[e];
+    const float2 u = uv[v.x];
+    int kr, kc;
+    float fr, fc;
+    split_kappa(u.x, ks, kr, fr);
+    split_kappa(u.y, ks, kc, fc);
+    out[e] = make_int4(v.x, v.y, __float_as_int(fr), __float_as_int(fc));
+  }
+}
+
 __global__ void k_fill_f32(int64_t n, float* p, float v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -204,7 +228,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_tile_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -221,6 +245,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   const int64_t M = c->M;
   float2* d_uv_user = nullptr;
   int2* d_k0 = nullptr;
+  int2* d_lk = nullptr;
   int st = PURIFY_OK;
   TRY(dev_alloc(&d_uv_user, M));
   if ((st = dev_alloc(&d_k0, M)) != PURIFY_OK) { cudaFree(d_uv_user); return st; }
@@ -278,6 +303,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
     if (t < 0) t += L;
     return t >= L - (J - 1) ? t - L : t;
   };
+  std::vector<int> lkey(c->nlist);
   {
     std::vector<std::pair<int, int>> seg;
     for (int t = 0; t < c->ntiles; ++t) {
@@ -290,14 +316,18 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       }
       std::stable_sort(seg.begin(), seg.end(),
                        [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
-      for (size_t k = 0; k < seg.size(); ++k) list[lcnt[t] + k] = seg[k].second;
+      for (size_t k = 0; k < seg.size(); ++k) {
+        list[lcnt[t] + k] = seg[k].second;
+        lkey[lcnt[t] + k] = seg[k].first;
+      }
     }
   }
-  // gridding work units: each tile's list in chunks that fit the kernel's
-  // shared memory (64 KB: start-cell offsets + key, value, 2J weights per entry)
+  // gridding work units: each tile's list in chunks whose entries, with the
+  // kernel's fixed tables, fit a shared-memory budget that keeps three CTAs
+  // resident per SM
   const int64_t mean = (c->nlist + c->ntiles - 1) / c->ntiles;
-  const int per_entry = 12 + 8 * J;
-  const int cap = std::max(128, ((65536 - (W * W + 1) * 4) / per_entry) / 128 * 128);
+  const int64_t room = (int64_t)purify::kGridSmemBudget - (int64_t)purify::grid_fixed_bytes(T, J);
+  const int cap = (int)std::max<int64_t>(128, room / (int64_t)purify::grid_entry_bytes(J) / 32 * 32);
   c->chunk_max = (int)std::min<int64_t>(cap, std::max<int64_t>(256, ((3 * mean / 2 + 127) / 128) * 128));
   std::vector<int4> chunks;
   std::vector<int> slot0(c->ntiles, -1), nchunk(c->ntiles, 0);
@@ -334,7 +364,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   std::stable_sort(dchunks.begin(), dchunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
   c->ndchunks = (int)dchunks.size();
   if ((st = dev_alloc(&c->d_uv, M)) == PURIFY_OK && (st = dev_alloc(&c->d_perm, M)) == PURIFY_OK &&
-      (st = dev_alloc(&c->d_tile_list, c->nlist)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_list, c->nlist)) == PURIFY_OK && (st = dev_alloc(&d_lk, c->nlist)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_chunks, c->nchunks)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_dchunks, std::max(1, c->ndchunks))) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_slot0, c->ntiles)) == PURIFY_OK &&
@@ -342,16 +372,24 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       (st = dev_alloc(&c->d_tile_cnt, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_slots, (size_t)std::max(1, nslots) * T * T)) == PURIFY_OK) {
     cudaMemcpyAsync(c->d_perm, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_tile_list, list.data(), c->nlist * sizeof(int), cudaMemcpyHostToDevice, s);
+    {
+      std::vector<int2> lk(c->nlist);
+      for (int64_t e = 0; e < c->nlist; ++e) lk[e] = make_int2(list[e], lkey[e]);
+      cudaMemcpyAsync(d_lk, lk.data(), c->nlist * sizeof(int2), cudaMemcpyHostToDevice, s);
+      launch_gather_perm(M, d_uv_user, c->d_perm, c->d_uv, s);
+      PURIFY_LAUNCH(c, "list_setup", s,
+                    (k_list_setup<<<nblk(c->nlist), 256, 0, s>>>(d_lk, c->d_uv, c->ks, c->nlist, c->d_list)));
+      if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
+    }
     cudaMemcpyAsync(c->d_chunks, chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
     if (c->ndchunks > 0)
       cudaMemcpyAsync(c->d_dchunks, dchunks.data(), c->ndchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_slot0, slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_nchunk, nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->d_tile_cnt, 0, c->ntiles * sizeof(unsigned), s);
-    launch_gather_perm(M, d_uv_user, c->d_perm, c->d_uv, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
   }
+  cudaFree(d_lk);
   cudaFree(d_uv_user);
   cudaFree(d_k0);
   return st;
@@ -468,6 +506,10 @@ const char* purify_status_string(int status) {
     case PURIFY_E_UNSUPPORTED: return "unsupported grid size";
     default: return "unknown status";
   }
+}
+
+const char* purify_last_error(void) {
+  return t_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(t_last_cuda_error);
 }
 
 int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purify_stream_t stream) {

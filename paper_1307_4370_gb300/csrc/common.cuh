@@ -196,6 +196,20 @@ extern std::atomic<unsigned long long> g_launches;
 // ---------------------------------------------------------------------------
 // The context (opaque to callers).
 // ---------------------------------------------------------------------------
+// Shared-memory layout of one gridding chunk (k_grid): per entry a start-cell
+// key, the value and the zero-padded row and column kernel weights (stride
+// kept odd against bank conflicts); per CTA the start-cell run offsets, the
+// prefix of the cell blocks' work and two partial-sum slots per thread.
+namespace purify {
+constexpr int kGridThreads = 256;
+__host__ __device__ constexpr int grid_wstride(int J) { return 2 * (J + 2) + 1; }
+__host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 4 + 8 + 4 * (size_t)grid_wstride(J); }
+__host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
+  return (size_t)2 * kGridThreads * 32 + (size_t)((T + J - 1) * (T + J - 1) + 1) * 4 + (size_t)((T / 2) * (T / 2) + 1) * 4;
+}
+constexpr size_t kGridSmemBudget = 72 * 1024;
+}  // namespace purify
+
 struct purify_ctx {
   int device;
   int n, L, J, levels, q;
@@ -217,7 +231,8 @@ struct purify_ctx {
   int tileT;            // tile side (cells)
   int tiles_1d;         // L / tileT
   int ntiles;
-  int* d_tile_list;     // sorted visibility indices whose footprint meets each tile, tile by tile
+  int4* d_list;         // per tile, the visibilities whose footprint meets it, by start cell:
+                        // (sorted index, start-cell key, kappa fractions of row and column as float bits)
   int64_t nlist;
   // gridding work units: each tile's list cut into chunks of at most chunk_max entries;
   // a tile with several chunks sums their partial tiles (slots) in chunk order

@@ -54,10 +54,11 @@ static FftShape col_shape(const purify_ctx* c) {
   return f;
 }
 
-// Dynamic shared memory above 48 KB needs a per-kernel opt-in.
+// Static plus dynamic shared memory above 48 KB needs a per-kernel opt-in
+// (the kernels' static shared memory is well under 8 KB).
 template <class K>
 static void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -211,23 +212,42 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
                                                 const int4* __restrict__ dchunks, KbPoly kb, KappaScale ks, int L,
                                                 int T, int tiles_1d, double* partials, DevScalars* sc) {
   extern __shared__ float2 halo[];
-  const int W = T + J - 1;
+  constexpr int NT = 256;
+  const int W = T + J - 1, NW = W * W;
   const int4 ch = dchunks[blockIdx.x];
   const int tr = ch.x / tiles_1d, tc = ch.x - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
-  for (int rr = threadIdx.x >> 5; rr < W; rr += blockDim.x >> 5) {
-    int r = R0 + rr;
-    if (r >= L) r -= L;
-    for (int cc = threadIdx.x & 31; cc < W; cc += 32) {
-      int c = C0 + cc;
-      if (c >= L) c -= L;
-      halo[rr * W + cc] = __ldg(&X[(size_t)r * L + c]);
+  // the first frequencies of this thread, in flight with the halo loads
+  constexpr int QV = 4;
+  float2 uq[QV];
+#pragma unroll
+  for (int q = 0; q < QV; ++q) {
+    const int i = ch.y + threadIdx.x + q * NT;
+    if (i < ch.z) uq[q] = __ldg(&uv[i]);
+  }
+  // halo of the tile: eight cells per thread per round, all loads issued first
+  for (int k0 = 0; k0 < NW; k0 += 8 * NT) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + threadIdx.x + q * NT;
+      if (k < NW) {
+        const int rr = k / W, cc = k - rr * W;  // W = T + J - 1 is not a Div form
+        int r = R0 + rr, c = C0 + cc;
+        if (r >= L) r -= L;
+        if (c >= L) c -= L;
+        v[q] = __ldg(&X[(size_t)r * L + c]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + threadIdx.x + q * NT;
+      if (k < NW) halo[k] = v[q];
     }
   }
   __syncthreads();
   FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
-  for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
-    const float2 u = __ldg(&uv[i]);
+  auto visit = [&](int i, float2 u) {
     int k0r, k0c;
     float fr, fc;
     split_kappa(u.x, ks, k0r, fr);
@@ -291,7 +311,13 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
       part[1].add_sq_diff(acc.x, y.x);
       part[1].add_sq_diff(acc.y, y.y);
     }
+  };
+#pragma unroll
+  for (int q = 0; q < QV; ++q) {
+    const int i = ch.y + threadIdx.x + q * NT;
+    if (i < ch.z) visit(i, uq[q]);
   }
+  for (int i = ch.y + threadIdx.x + QV * NT; i < ch.z; i += NT) visit(i, __ldg(&uv[i]));
   if (MODE == kDegridSdmm) {
     double acc2[2] = {part[0].value(), part[1].value()};
     double tot[2];
@@ -310,138 +336,273 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // set-up listed, per tile, the visibilities whose footprint meets it, sorted
 // by the footprint's first cell relative to the tile (one run per start
 // cell), and cut each list into chunks.  One CTA per chunk stages its
-// entries (start cell, value, J + J kernel weights) in shared memory; each
-// thread owns a 2 x 2 block of cells and sums, in a fixed order, the entries
-// of the (J + 1)^2 start cells whose footprint reaches it.  A tile with one
-// chunk is written to X directly; otherwise each chunk stores a partial tile
-// and the last chunk to finish adds the partials in chunk order.  Every cell
-// is written once and the result does not depend on scheduling.
+// entries (start cell, value, J + J kernel weights) in shared memory.  A
+// 2 x 2 block of cells ("owner") sums, in a fixed order, the entries of the
+// (J + 1)^2 start cells whose footprint reaches it: J + 1 runs of the sorted
+// list, one per start row.  The owners' work is uneven (dense start cells
+// where tracks cross), so the CTA splits the concatenation of all owners'
+// runs into equal slices, one per thread (merge-path style): a thread writes
+// the owners that lie inside its slice and leaves two partial sums for the
+// owners cut by its slice ends, which are added afterwards in slice order.
+// A tile with one chunk is written to X directly; otherwise each chunk
+// stores a partial tile and the last chunk to finish adds the partials in
+// chunk order.  Every cell is written once and the result does not depend
+// on scheduling.
 // ---------------------------------------------------------------------------
+// Exclusive prefix sum of one int per thread over the block (blockDim a
+// multiple of 32); *total gets the block sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int x = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane < nw) wsum[lane] = x;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int excl = incl - v + (wid > 0 ? wsum[wid - 1] : 0);
+  *total = wsum[nw - 1];
+  __syncthreads();
+  return excl;
+}
+
+struct Acc4 {  // a 2 x 2 block of complex sums
+  float2 a00, a01, a10, a11;
+};
+
 template <int J, int MODE>
-__global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
-                                              const int* __restrict__ perm, const float2* __restrict__ vis,
-                                              const int* __restrict__ tile_list, const int4* __restrict__ chunks,
-                                              const int* __restrict__ tile_slot0, const int* __restrict__ tile_nchunk,
-                                              unsigned* __restrict__ tile_cnt, float2* __restrict__ slots, KbPoly kb,
-                                              KappaScale ks, int L, int T, int tiles_1d, int chunk_max) {
+__global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
+                                                       const int* __restrict__ perm, const float2* __restrict__ vis,
+                                                       const int4* __restrict__ list,
+                                                       const int4* __restrict__ chunks,
+                                                       const int* __restrict__ tile_slot0,
+                                                       const int* __restrict__ tile_nchunk,
+                                                       unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
+                                                       KbPoly kb, KappaScale ks, int L, int T, int tiles_1d,
+                                                       int chunk_max) {
+  constexpr int NT = kGridThreads;
+  constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
   extern __shared__ float4 sm4[];
   __shared__ bool s_last;
-  const int W = T + J - 1;
-  const int NK = W * W;
-  float2* yv = reinterpret_cast<float2*>(sm4);                 // chunk_max values
-  float* wt = reinterpret_cast<float*>(yv + chunk_max);        // chunk_max x 2J weights
-  int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * 2 * J);  // chunk_max keys
-  int* off = key + chunk_max;                                  // NK + 1 run offsets
+  __shared__ int wsum[NT / 32];
+  const int W = T + J - 1, NK = W * W, HB = T / 2, NO = HB * HB;
+  const int lhb = __ffs(HB) - 1;  // T is a power of two
+  float4* part = sm4;                                   // slot j: first[j] at 4j, last[j] at 4j + 2
+  float2* yv = reinterpret_cast<float2*>(part + 4 * NT);
+  float* wt = reinterpret_cast<float*>(yv + chunk_max);
+  int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);
+  int* off = key + chunk_max;  // NK + 1 run offsets
+  int* P = off + NK + 1;       // NO + 1 work prefix of the owners
   const int4 ch = chunks[blockIdx.x];
   const int tile = ch.x;
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
   const int ne = ch.z - ch.y;
-  // stage the chunk's entries
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const int i = tile_list[ch.y + e];
-    const float2 u = __ldg(&uv[i]);
-    const float2 val = (MODE == kGridPerm) ? __ldg(&vis[perm[i]]) : __ldg(&vis[i]);
-    int k0r, k0c;
-    float fr, fc;
-    split_kappa(u.x, ks, k0r, fr);
-    split_kappa(u.y, ks, k0c, fc);
-    k0r -= J / 2 - 1;
-    k0c -= J / 2 - 1;
-    float wr[J], wc[J];
-    kb_weights<J>(kb, fr, wr);
-    kb_weights<J>(kb, fc, wc);
-    int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
-    if (dr >= L - (J - 1)) dr -= L;
-    if (dc >= L - (J - 1)) dc -= L;
-    const bool inside = dr < T && dc < T;  // always, for a consistent table
-    key[e] = inside ? (dr + J - 1) * W + (dc + J - 1) : NK;
-    yv[e] = val;
+  // ---- stage the chunk's entries (loads of four entries per thread in flight)
+  for (int e0 = 0; e0 < ne; e0 += 4 * NT) {
+    int4 le[4];
+    float2 val[4];
 #pragma unroll
-    for (int k = 0; k < J; ++k) {
-      wt[e * 2 * J + k] = wr[k];
-      wt[e * 2 * J + J + k] = wc[k];
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + threadIdx.x + q * NT;
+      le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
     }
-  }
-  __syncthreads();
-  // off[k] = first entry with key >= k = number of entries with key < k:
-  // count the entries of each key, then an exclusive prefix sum over the keys
-  // (each thread owns a contiguous run of keys; balanced whatever the density)
-  for (int k = threadIdx.x; k <= NK; k += blockDim.x) off[k] = 0;
-  __syncthreads();
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) atomicAdd(&off[key[e]], 1);
-  __syncthreads();
-  {
-    __shared__ int wsum[32];
-    const int per = (NK + 1 + blockDim.x - 1) / blockDim.x;
-    const int k0 = threadIdx.x * per, k1 = min(k0 + per, NK + 1);
-    int run = 0;
-    for (int k = k0; k < k1; ++k) run += off[k];
-    // exclusive scan of the runs across the block
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = run;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      const int nw = blockDim.x >> 5;
-      int v = lane < nw ? wsum[lane] : 0;
+    for (int q = 0; q < 4; ++q)
+      if (le[q].x >= 0) val[q] = (MODE == kGridPerm) ? __ldg(&vis[__ldg(&perm[le[q].x])]) : __ldg(&vis[le[q].x]);
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
+    for (int q = 0; q < 4; ++q) {
+      if (le[q].x < 0) continue;
+      const int e = e0 + threadIdx.x + q * NT;
+      float wr[J], wc[J];
+      kb_weights<J>(kb, __int_as_float(le[q].z), wr);
+      kb_weights<J>(kb, __int_as_float(le[q].w), wc);
+      key[e] = le[q].y;
+      yv[e] = val[q];
+      float* w = wt + (size_t)e * S;
+      w[0] = 0.f;
+      w[J + 1] = 0.f;
+      w[J + 2] = 0.f;
+      w[2 * J + 3] = 0.f;
+#pragma unroll
+      for (int k = 0; k < J; ++k) {
+        w[1 + k] = wr[k];
+        w[J + 3 + k] = wc[k];
       }
-      if (lane < nw) wsum[lane] = v;  // inclusive warp totals
-    }
-    __syncthreads();
-    int base = incl - run + (wid > 0 ? wsum[wid - 1] : 0);
-    for (int k = k0; k < k1; ++k) {
-      const int cnt = off[k];
-      off[k] = base;
-      base += cnt;
     }
   }
   __syncthreads();
-  const int HB = T / 2;
+  // ---- off[k] = first entry with key >= k (keys are sorted): binary searches,
+  // each thread a contiguous run of keys
+  {
+    const int per = (NK + 1 + NT - 1) / NT;
+    const int k0 = threadIdx.x * per, k1 = min(k0 + per, NK + 1);
+    int lo = 0;
+    for (int k = k0; k < k1; ++k) {
+      int hi = ne;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid] < k) lo = mid + 1;
+        else hi = mid;
+      }
+      off[k] = lo;
+    }
+  }
+  __syncthreads();
+  // ---- work of each owner (entries over its J + 1 runs), prefix over owners
+  int Wt;
+  {
+    constexpr int kMaxPer = 4;  // owners per thread: (T / 2)^2 / 256 <= 4 for T <= 64
+    const int per = (NO + NT - 1) / NT;
+    const int o0 = threadIdx.x * per;
+    int cnt[kMaxPer];
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+      const int o = o0 + q;
+      cnt[q] = 0;
+      if (q < per && o < NO) {
+        const int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
+        for (int kr = R; kr <= R + J; ++kr) cnt[q] += off[kr * W + C + J + 1] - off[kr * W + C];
+      }
+      run += cnt[q];
+    }
+    int base = block_excl_scan(run, wsum, &Wt);
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+      const int o = o0 + q;
+      if (q < per && o < NO) {
+        P[o] = base;
+        base += cnt[q];
+      }
+    }
+    if (threadIdx.x == 0) P[NO] = Wt;
+  }
+  __syncthreads();
   const bool multi = ch.w >= 0;
   float2* dst = multi ? slots + (size_t)ch.w * T * T : nullptr;
-  for (int blk = threadIdx.x; blk < HB * HB; blk += blockDim.x) {
-    const int R = 2 * (blk / HB), C = 2 * (blk - (blk / HB) * HB);
-    float2 acc00 = make_float2(0.f, 0.f), acc01 = acc00, acc10 = acc00, acc11 = acc00;
-    // start rows sr in [R - J + 1, R + 1], i.e. key rows R .. R + J
-    for (int kr = R; kr <= R + J; ++kr) {
-      const int a0 = R + J - 1 - kr;  // row tap of cell row R (valid if 0 <= a0 < J)
-      const int kbase = kr * W;
-      const int e0 = off[kbase + C], e1 = off[kbase + C + J + 1];  // key cols C .. C + J
-      for (int e = e0; e < e1; ++e) {
-        const int kc = key[e] - kbase;
-        const int b0 = C + J - 1 - kc;  // column tap of cell column C
-        const float2 v = yv[e];
-        const float* w = wt + e * 2 * J;
-        const float wc0 = (b0 >= 0 && b0 < J) ? w[J + b0] : 0.f;
-        const float wc1 = (b0 + 1 >= 0 && b0 + 1 < J) ? w[J + b0 + 1] : 0.f;
-        const float wr0 = (a0 >= 0 && a0 < J) ? w[a0] : 0.f;
-        const float wr1 = (a0 + 1 >= 0 && a0 + 1 < J) ? w[a0 + 1] : 0.f;
-        const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
-        acc00.x = fmaf(wc0, v0.x, acc00.x); acc00.y = fmaf(wc0, v0.y, acc00.y);
-        acc01.x = fmaf(wc1, v0.x, acc01.x); acc01.y = fmaf(wc1, v0.y, acc01.y);
-        acc10.x = fmaf(wc0, v1.x, acc10.x); acc10.y = fmaf(wc0, v1.y, acc10.y);
-        acc11.x = fmaf(wc1, v1.x, acc11.x); acc11.y = fmaf(wc1, v1.y, acc11.y);
-      }
-    }
+  auto write_owner = [&](int o, const Acc4& a) {
+    const int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
     if (!multi) {
       float2* row0 = X + (size_t)(R0 + R) * L + C0 + C;
-      float2* row1 = row0 + L;
-      reinterpret_cast<float4*>(row0)[0] = make_float4(acc00.x, acc00.y, acc01.x, acc01.y);
-      reinterpret_cast<float4*>(row1)[0] = make_float4(acc10.x, acc10.y, acc11.x, acc11.y);
+      reinterpret_cast<float4*>(row0)[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
+      reinterpret_cast<float4*>(row0 + L)[0] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
     } else {
-      reinterpret_cast<float4*>(dst + R * T + C)[0] = make_float4(acc00.x, acc00.y, acc01.x, acc01.y);
-      reinterpret_cast<float4*>(dst + (R + 1) * T + C)[0] = make_float4(acc10.x, acc10.y, acc11.x, acc11.y);
+      reinterpret_cast<float4*>(dst + R * T + C)[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
+      reinterpret_cast<float4*>(dst + (R + 1) * T + C)[0] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
     }
+  };
+  // ---- this thread's slice [t0, t1) of the concatenated runs, walked as one
+  // flat loop (one entry per step) so the lanes of a warp stay in step
+  const int j = threadIdx.x;
+  const int t0 = (j * Wt + NT - 1) / NT, t1 = ((j + 1) * Wt + NT - 1) / NT;
+  const int nmy = t1 - t0;
+  if (nmy > 0) {
+    int o = 0;  // owner holding t0: the last o with P[o] <= t0
+    {
+      int hi = NO - 1;
+      while (o < hi) {
+        const int mid = (o + hi + 1) >> 1;
+        if (P[mid] <= t0) o = mid;
+        else hi = mid - 1;
+      }
+    }
+    int Po = P[o], Pe = P[o + 1];
+    int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
+    int kr = R, ee = 0, run_end = 0;
+    for (int local = t0 - Po;; ++kr) {  // the run of o holding t0
+      const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
+      if (local < s1 - s0) {
+        ee = s0 + local;
+        run_end = s1;
+        break;
+      }
+      local -= s1 - s0;
+    }
+    int a0 = R + J - 1 - kr, kbase = kr * W;  // row taps of cell rows R, R + 1: padded index a0 + 1, a0 + 2
+    Acc4 a;
+    a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
+    auto flush = [&]() {
+      if (Po >= t0 && Pe <= t1) {
+        write_owner(o, a);
+      } else {
+        float4* sl = part + 4 * j + (Po < t0 ? 0 : 2);  // first / last owner of the slice
+        sl[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
+        sl[1] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
+      }
+    };
+    for (int step = 0; step < nmy; ++step) {
+      const int b0 = C + J - 1 - (key[ee] - kbase);  // column tap of cell column C, in [-1, J - 1]
+      const float2 v = yv[ee];
+      const float* w = wt + ee * S;
+      const float wr0 = w[a0 + 1], wr1 = w[a0 + 2];
+      const float wc0 = w[J + 3 + b0], wc1 = w[J + 4 + b0];
+      const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
+      a.a00.x = fmaf(wc0, v0.x, a.a00.x); a.a00.y = fmaf(wc0, v0.y, a.a00.y);
+      a.a01.x = fmaf(wc1, v0.x, a.a01.x); a.a01.y = fmaf(wc1, v0.y, a.a01.y);
+      a.a10.x = fmaf(wc0, v1.x, a.a10.x); a.a10.y = fmaf(wc0, v1.y, a.a10.y);
+      a.a11.x = fmaf(wc1, v1.x, a.a11.x); a.a11.y = fmaf(wc1, v1.y, a.a11.y);
+      if (++ee == run_end && step + 1 < nmy) {
+        // next non-empty run of this owner, else the next owner with work
+        for (;;) {
+          if (++kr > R + J) {
+            flush();
+            a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
+            do {
+              ++o;
+              Po = Pe;
+              Pe = P[o + 1];
+            } while (Pe == Po);
+            R = 2 * (o >> lhb);
+            C = 2 * (o & (HB - 1));
+            kr = R;
+          }
+          const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
+          if (s1 > s0) {
+            ee = s0;
+            run_end = s1;
+            break;
+          }
+        }
+        a0 = R + J - 1 - kr;
+        kbase = kr * W;
+      }
+    }
+    flush();
+  }
+  __syncthreads();
+  // ---- owners cut by slice ends (sum in slice order) and owners with no work
+  for (int o = threadIdx.x; o < NO; o += NT) {
+    const int Po = P[o], Pe = P[o + 1];
+    Acc4 a;
+    a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
+    if (Pe > Po) {
+      const int ja = (Po * NT) / Wt, jb = ((Pe - 1) * NT) / Wt;
+      if (ja == jb) continue;  // written by its slice
+      float4 p0 = part[4 * ja + 2], p1 = part[4 * ja + 3];
+      for (int jj = ja + 1; jj <= jb; ++jj) {
+        if ((jj * Wt + NT - 1) / NT == ((jj + 1) * Wt + NT - 1) / NT) continue;  // empty slice
+        const float4 q0 = part[4 * jj], q1 = part[4 * jj + 1];
+        p0 = make_float4(p0.x + q0.x, p0.y + q0.y, p0.z + q0.z, p0.w + q0.w);
+        p1 = make_float4(p1.x + q1.x, p1.y + q1.y, p1.z + q1.z, p1.w + q1.w);
+      }
+      a.a00 = make_float2(p0.x, p0.y);
+      a.a01 = make_float2(p0.z, p0.w);
+      a.a10 = make_float2(p1.x, p1.y);
+      a.a11 = make_float2(p1.z, p1.w);
+    }
+    write_owner(o, a);
   }
   if (!multi) return;
   __threadfence();
@@ -453,9 +614,9 @@ __global__ void __launch_bounds__(256) k_grid(float2* __restrict__ X, const floa
   __threadfence();
   const int TT = T * T;
   const float2* first = slots + (size_t)tile_slot0[tile] * TT;
-  for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+  for (int k = threadIdx.x; k < TT; k += NT) {
     float2 sum = make_float2(0.f, 0.f);
-    for (int j = 0; j < nc; ++j) sum = cadd(sum, __ldcg(&first[(size_t)j * TT + k]));
+    for (int c = 0; c < nc; ++c) sum = cadd(sum, __ldcg(&first[(size_t)c * TT + k]));
     const int rr = k / T, cc = k - rr * T;
     X[(size_t)(R0 + rr) * L + C0 + cc] = sum;
   }
@@ -683,23 +844,20 @@ int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
 
 template <int J>
 static size_t grid_smem(const purify_ctx* c) {
-  const int W = c->tileT + J - 1;
-  return (size_t)c->chunk_max * (8 + 8 * J + 4) + (size_t)(W * W + 1) * 4;
+  return grid_fixed_bytes(c->tileT, J) + (size_t)c->chunk_max * grid_entry_bytes(J);
 }
 
 template <int J>
 static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
-  const int HB = c->tileT / 2;
-  const int threads = HB * HB < 64 ? 64 : (HB * HB > 256 ? 256 : HB * HB);
   const size_t sm = grid_smem<J>(c);
 #define GRD(MD)                                                                                                \
   do {                                                                                                         \
     allow_smem(k_grid<J, MD>, sm);                                                                             \
     PURIFY_LAUNCH(c, "grid", s,                                                                                \
-                  (k_grid<J, MD><<<c->nchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, vis, c->d_tile_list, \
-                                                                 c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
-                                                                 c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L,       \
-                                                                 c->tileT, c->tiles_1d, c->chunk_max)));             \
+                  (k_grid<J, MD><<<c->nchunks, kGridThreads, sm, s>>>(                                         \
+                      c->d_grid, c->d_uv, c->d_perm, vis, c->d_list, c->d_chunks, c->d_tile_slot0,        \
+                      c->d_tile_nchunk, c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d,  \
+                      c->chunk_max)));                                                                         \
   } while (0)
   if (mode == kGridPerm) GRD(kGridPerm);
   else GRD(kGridSorted);

@@ -58,23 +58,28 @@ def test_phi_and_adjoint(n, M, J, kind):
 
 
 def test_phi_large_sampled():
-    """1024 x 1024, M = 2^21 (the mixed-precision workload's sizes), all outputs."""
+    """1024 x 1024, M = 2^21 (the mixed-precision workload's sizes), all outputs,
+    for every tile side the autotuner may pick (dense arcs give multi-chunk
+    tiles and the largest shared-memory footprints)."""
     torch = require_gpu()
-    from paper_1307_4370_gb300 import binding
+    from paper_1307_4370_gb300 import autotune, binding
 
     p = inputs.make_problem("sdmm1024")
     w = p.workload
     rng = np.random.default_rng(3)
     x = inputs.random_image(w.n, rng)
-    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
-    y = host(ctx.phi(dev(x, torch)))
     idx = rng.choice(w.M, 20000, replace=False)
     want = me.phi(x, p.uv, w.J)
-    assert rel_err(y, want) <= TOL
-    assert rel_err(y[idx], want[idx]) <= TOL
     v = inputs.random_vis(w.M, rng)
-    xa = host(ctx.phi_adj(dev(v, torch)))
-    assert rel_err(xa, me.phi_adj(v, p.uv, w.n, w.J)) <= TOL
+    want_adj = me.phi_adj(v, p.uv, w.n, w.J)
+    for t in autotune.valid_tiles(w.n, w.J):
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J, tile=t)
+        y = host(ctx.phi(dev(x, torch)))
+        assert rel_err(y, want) <= TOL
+        assert rel_err(y[idx], want[idx]) <= TOL
+        xa = host(ctx.phi_adj(dev(v, torch)))
+        assert rel_err(xa, want_adj) <= TOL
+        ctx.close()
 
 
 @pytest.mark.parametrize("n,levels,mask", [(16, 4, 0x1FF), (64, 4, 0x1FF), (96, 4, 0x1FF), (192, 4, 0x1FF),
