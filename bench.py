@@ -189,6 +189,31 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
     }
 
 
+KERNEL_SOURCE = {"row_fwd": "nufft.cu", "col_fwd": "nufft.cu", "degrid": "nufft.cu", "grid": "nufft.cu",
+                 "col_inv": "nufft.cu", "row_inv": "nufft.cu", "dwt_level": "sara.cu", "idwt_level": "sara.cu",
+                 "dirac": "sara.cu", "sdmm_l2": "vecops.cu"}
+
+
+def dram_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this
+    workload, or None when there is none or the kernel's source file changed
+    after the capture (the record carries the file's SHA-256)."""
+    import hashlib
+
+    src = KERNEL_SOURCE.get(kernel)
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if src is None or not os.path.exists(path):
+        return None
+    with open(os.path.join(ROOT, "paper_1307_4370_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    with open(path) as f:
+        for ln in f:
+            parts = ln.split()
+            if len(parts) == 4 and not ln.startswith("#") and parts[0] == workload and parts[1] == kernel:
+                return int(parts[2]) if parts[3] == sha else None
+    return None
+
+
 def peaks() -> tuple[float, str]:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -360,7 +385,7 @@ def run_gpu(args, w):
             "phi_phiadj": {"value": gvis, "unit": "Gvis/s", "ms": phi_ms},
             "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "alg_bytes_per_launch": abytes.get(dom[0]),
+                         "traffic": dram_traffic(w.name, dom[0]), "alg_bytes_per_launch": abytes.get(dom[0]),
                          "us_per_launch": per_launch_s * 1e6},
             "kernels": kernels,
             "cpu_baseline": cpu_entry,

@@ -1,4 +1,5 @@
-"""The multi-rank host logic of bench.py on two gloo ranks (no GPU).
+"""Host logic of bench.py without a GPU: the multi-rank path on two gloo ranks
+and the roofline's traffic record.
 
 Under torchrun every rank solves its own problem (weak scaling, no collective
 on the data path); the ranks only agree on the slowest time.  The reference
@@ -50,3 +51,25 @@ def test_reference_arm_prints_on_rank_zero_only(capsys, monkeypatch):
     ns = type("Args", (), {"steps": 1, "warmup": 0, "gpus": 2})()
     bench.run_reference(ns, bench.inputs.WORKLOADS["sdmm64"])
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu record and turns
+    to null when the kernel's source file no longer matches the record."""
+    import hashlib
+
+    import bench
+
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    csrc = tmp_path / "paper_1307_4370_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "nufft.cu").write_text("kernel v1\n")
+    sha = hashlib.sha256(b"kernel v1\n").hexdigest()
+    (prof / "dram_traffic.txt").write_text(f"# comment\nsdmm256 grid 1234 {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.dram_traffic("sdmm256", "grid") == 1234
+    assert bench.dram_traffic("sdmm1024", "grid") is None
+    assert bench.dram_traffic("sdmm256", "nosuch") is None
+    (csrc / "nufft.cu").write_text("kernel v2\n")
+    assert bench.dram_traffic("sdmm256", "grid") is None
