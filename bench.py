@@ -176,8 +176,11 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
         # write p, s, x, r (single-reduction CG update); always write n x 2n rows
         "row_fwd": ((3 + (k - 1) * 11 + 11) * N * c) / (k + 1),
         "col_fwd": 6 * N * c,                          # read n x 2n, write 2n x 2n
-        "degrid": (k * (4 * N * c + 2 * M * c) + (4 * N * c + 4 * M * c)) / (k + 1),
+        "degrid": 4 * N * c + 4 * M * c,               # SDMM: read grid, uv, z2, y; write s2
         "grid": 4 * N * c + 2 * M * c,                 # read uv + vis, write the grid
+        # CG steps, G^T G in one pass: read the grid and the list entries
+        # (16 B = 2c per visibility), write the second grid
+        "gram": 8 * N * c + 2 * M * c,
         "col_inv": 6 * N * c,
         # CG: read n x 2n rows and r, write w; SDMM: also x_hat, z3, x1 in, z3 out
         "row_inv": (k * 4 * N * c + 7 * N * c) / (k + 1),
@@ -190,6 +193,7 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
 
 
 KERNEL_SOURCE = {"row_fwd": "nufft.cu", "col_fwd": "nufft.cu", "degrid": "nufft.cu", "grid": "nufft.cu",
+                 "gram": "nufft.cu",
                  "col_inv": "nufft.cu", "row_inv": "nufft.cu", "dwt_level": "sara.cu", "idwt_level": "sara.cu",
                  "dirac": "sara.cu", "sdmm_l2": "vecops.cu"}
 

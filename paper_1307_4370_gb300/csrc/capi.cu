@@ -230,7 +230,7 @@ void free_ctx(purify_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
-                  c->d_grid, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
+                  c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -408,14 +408,11 @@ int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, float2* 
   ia.s = sv;
   ia.w = w;
   TRY(phi_forward_grid(c, first ? kRowInPlain : kRowInCgUpd, ia, s));
-  DegridArgs da{};
-  da.out = c->d_vis;
-  TRY(degrid(c, kDegridSorted, da, s));
-  TRY(grid_adjoint(c, kGridSorted, c->d_vis, s));
+  TRY(gram_grid(c, s));  // G^T G in one pass (the M samples are not stored)
   RowOutArgs ra{};
   ra.out = w;
   ra.p = r;
-  return phi_adjoint_image(c, kRowOutCgQ, ra, s);
+  return phi_adjoint_image(c, kRowOutCgQ, ra, s, c->d_grid2);
 }
 
 int64_t ctx_N(const purify_ctx* c) { return (int64_t)c->n * c->n; }
@@ -558,7 +555,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   int st = PURIFY_OK;
   auto fail = [&](int code) { free_ctx(c); return code; };
   if ((st = dev_alloc(&c->d_deapod, c->n)) || (st = dev_alloc(&c->d_tw, c->L)) ||
-      (st = dev_alloc(&c->d_grid, (size_t)c->L * c->L)) || (st = dev_alloc(&c->d_half, (size_t)c->n * c->L)) ||
+      (st = dev_alloc(&c->d_grid, (size_t)c->L * c->L)) || (st = dev_alloc(&c->d_grid2, (size_t)c->L * c->L)) || (st = dev_alloc(&c->d_half, (size_t)c->n * c->L)) ||
       (st = dev_alloc(&c->d_vis, c->M)) || (st = dev_alloc(&c->d_vis2, c->M)) ||
       (st = dev_alloc(&c->d_ll[0], c->q * n2)) || (st = dev_alloc(&c->d_ll[1], c->q * n2)) ||
       (st = dev_alloc(&c->d_img[0], N)) || (st = dev_alloc(&c->d_img[1], N)) || (st = dev_alloc(&c->d_img[2], N)) ||

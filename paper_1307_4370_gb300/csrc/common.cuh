@@ -204,8 +204,17 @@ namespace purify {
 constexpr int kGridThreads = 256;
 __host__ __device__ constexpr int grid_wstride(int J) { return 2 * (J + 2) + 1; }
 __host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 4 + 8 + 4 * (size_t)grid_wstride(J); }
+// The partial-sum slots share their space with the grid halo that the Gram
+// form (G^T G in one pass) stages before the entries.
+__host__ __device__ constexpr size_t grid_halo_bytes(int T, int J) {
+  return (size_t)(T + 2 * (J - 1)) * (T + 2 * (J - 1)) * 8;
+}
+__host__ __device__ constexpr size_t grid_slot_bytes(int T, int J) {
+  return grid_halo_bytes(T, J) > (size_t)2 * kGridThreads * 32 ? (grid_halo_bytes(T, J) + 15) / 16 * 16
+                                                                : (size_t)2 * kGridThreads * 32;
+}
 __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
-  return (size_t)2 * kGridThreads * 32 + (size_t)((T + J - 1) * (T + J - 1) + 1) * 4 + (size_t)((T / 2) * (T / 2) + 1) * 4;
+  return grid_slot_bytes(T, J) + (size_t)((T + J - 1) * (T + J - 1) + 1) * 4 + (size_t)((T / 2) * (T / 2) + 1) * 4;
 }
 constexpr size_t kGridSmemBudget = 72 * 1024;
 }  // namespace purify
@@ -250,6 +259,7 @@ struct purify_ctx {
 
   // scratch
   float2* d_grid;       // L x L
+  float2* d_grid2;      // L x L: output of the Gram pass (G^T G reads d_grid)
   float2* d_half;       // n x L (rows of the image after the row pass)
   float2* d_vis;        // M (sorted order)
   float2* d_vis2;       // M
@@ -338,7 +348,7 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s);  //
 // kRowInCgFinish: apply it, then transform x.
 enum RowInMode { kRowInPlain = 0, kRowInCgUpd = 1, kRowInCgFinish = 2 };
 enum DegridOut { kDegridPerm = 0, kDegridSorted = 1, kDegridSdmm = 2 };
-enum GridIn { kGridPerm = 0, kGridSorted = 1 };
+enum GridIn { kGridPerm = 0, kGridSorted = 1, kGridGram = 2 };
 enum RowOutMode { kRowOutPlain = 0, kRowOutCgQ = 1, kRowOutSdmm = 2 };
 
 struct RowInArgs {
@@ -368,7 +378,9 @@ struct RowOutArgs {
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s);
 int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s);
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s);
-int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s);
+int gram_grid(purify_ctx* c, cudaStream_t s);
+int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s,
+                      const float2* grid = nullptr);
 
 // sara.cu
 enum SaraMode { kSaraPlain = 0, kSaraProx = 1 };

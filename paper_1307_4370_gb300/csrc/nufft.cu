@@ -382,7 +382,7 @@ struct Acc4 {  // a 2 x 2 block of complex sums
 };
 
 template <int J, int MODE>
-__global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X, const float2* __restrict__ uv,
+__global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X, const float2* __restrict__ Xin,
                                                        const int* __restrict__ perm, const float2* __restrict__ vis,
                                                        const int4* __restrict__ list,
                                                        const int4* __restrict__ chunks,
@@ -398,8 +398,8 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X
   __shared__ int wsum[NT / 32];
   const int W = T + J - 1, NK = W * W, HB = T / 2, NO = HB * HB;
   const int lhb = __ffs(HB) - 1;  // T is a power of two
-  float4* part = sm4;                                   // slot j: first[j] at 4j, last[j] at 4j + 2
-  float2* yv = reinterpret_cast<float2*>(part + 4 * NT);
+  float4* part = sm4;  // slot j: first[j] at 4j, last[j] at 4j + 2 (Gram form: the halo first)
+  float2* yv = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm4) + grid_slot_bytes(T, J));
   float* wt = reinterpret_cast<float*>(yv + chunk_max);
   int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);
   int* off = key + chunk_max;  // NK + 1 run offsets
@@ -409,6 +409,35 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
   const int ne = ch.z - ch.y;
+  // ---- Gram form (G^T G): stage the (T + 2J - 2)^2 grid cells that the
+  // footprints of the tile's entries cover; each entry's value is then its
+  // degridded sample, in the same order of operations as k_degrid
+  const int HW = T + 2 * (J - 1);
+  float2* halo = reinterpret_cast<float2*>(sm4);
+  if constexpr (MODE == kGridGram) {
+    for (int k0 = 0; k0 < HW * HW; k0 += 8 * NT) {
+      float2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + threadIdx.x + q * NT;
+        if (k < HW * HW) {
+          const int rr = k / HW, cc = k - rr * HW;
+          int r = R0 - (J - 1) + rr, c = C0 - (J - 1) + cc;
+          if (r < 0) r += L;
+          if (r >= L) r -= L;
+          if (c < 0) c += L;
+          if (c >= L) c -= L;
+          v[q] = __ldg(&Xin[(size_t)r * L + c]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + threadIdx.x + q * NT;
+        if (k < HW * HW) halo[k] = v[q];
+      }
+    }
+    __syncthreads();
+  }
   // ---- stage the chunk's entries (loads of four entries per thread in flight)
   for (int e0 = 0; e0 < ne; e0 += 4 * NT) {
     int4 le[4];
@@ -418,9 +447,11 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X
       const int e = e0 + threadIdx.x + q * NT;
       le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
     }
+    if constexpr (MODE != kGridGram) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (le[q].x >= 0) val[q] = (MODE == kGridPerm) ? __ldg(&vis[__ldg(&perm[le[q].x])]) : __ldg(&vis[le[q].x]);
+      for (int q = 0; q < 4; ++q)
+        if (le[q].x >= 0) val[q] = (MODE == kGridPerm) ? __ldg(&vis[__ldg(&perm[le[q].x])]) : __ldg(&vis[le[q].x]);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (le[q].x < 0) continue;
@@ -428,6 +459,24 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X
       float wr[J], wc[J];
       kb_weights<J>(kb, __int_as_float(le[q].z), wr);
       kb_weights<J>(kb, __int_as_float(le[q].w), wc);
+      if constexpr (MODE == kGridGram) {
+        const int kr = le[q].y / W, kc = le[q].y - kr * W;  // footprint start in the halo
+        const float2* base = halo + kr * HW + kc;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int aa = 0; aa < J; ++aa) {
+          float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int b = 0; b < J; ++b) {
+            const float2 g = base[aa * HW + b];
+            t.x = fmaf(wc[b], g.x, t.x);
+            t.y = fmaf(wc[b], g.y, t.y);
+          }
+          acc.x = fmaf(wr[aa], t.x, acc.x);
+          acc.y = fmaf(wr[aa], t.y, acc.y);
+        }
+        val[q] = acc;
+      }
       key[e] = le[q].y;
       yv[e] = val[q];
       float* w = wt + (size_t)e * S;
@@ -850,19 +899,22 @@ static size_t grid_smem(const purify_ctx* c) {
 template <int J>
 static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
   const size_t sm = grid_smem<J>(c);
-#define GRD(MD)                                                                                                \
+#define GRD(MD, NAME, OUT, IN)                                                                                 \
   do {                                                                                                         \
     allow_smem(k_grid<J, MD>, sm);                                                                             \
-    PURIFY_LAUNCH(c, "grid", s,                                                                                \
+    PURIFY_LAUNCH(c, NAME, s,                                                                                  \
                   (k_grid<J, MD><<<c->nchunks, kGridThreads, sm, s>>>(                                         \
-                      c->d_grid, c->d_uv, c->d_perm, vis, c->d_list, c->d_chunks, c->d_tile_slot0,        \
-                      c->d_tile_nchunk, c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d,  \
-                      c->chunk_max)));                                                                         \
+                      OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
+                      c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max)));   \
   } while (0)
-  if (mode == kGridPerm) GRD(kGridPerm);
-  else GRD(kGridSorted);
+  if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
+  else if (mode == kGridSorted) GRD(kGridSorted, "grid", c->d_grid, nullptr);
+  else GRD(kGridGram, "gram", c->d_grid2, c->d_grid);
 #undef GRD
 }
+
+// G^T G of the grid in d_grid into d_grid2 (one pass; the M samples are not stored).
+int gram_grid(purify_ctx* c, cudaStream_t s) { return grid_adjoint(c, kGridGram, nullptr, s); }
 
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
   switch (c->J) {
@@ -874,7 +926,8 @@ int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) 
   return check_cuda(cudaGetLastError());
 }
 
-int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s) {
+int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* grid) {
+  const float2* Xg = grid ? grid : c->d_grid;
   const FftShape rs = row_shape(c), cs = col_shape(c);
   const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
   const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);
@@ -882,11 +935,11 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
   if (cs.ept == 8) {
     allow_smem(k_col_inv<8>, smc);
     PURIFY_LAUNCH(c, "col_inv", s,
-                  (k_col_inv<8><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
+                  (k_col_inv<8><<<gc, cs.threads, smc, s>>>(Xg, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
   } else {
     allow_smem(k_col_inv<12>, smc);
     PURIFY_LAUNCH(c, "col_inv", s,
-                  (k_col_inv<12><<<gc, cs.threads, smc, s>>>(c->d_grid, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
+                  (k_col_inv<12><<<gc, cs.threads, smc, s>>>(Xg, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
   }
 #define ROWI(E, MD)                                                                                          \
   do {                                                                                                       \
