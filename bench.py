@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--workload", default="sdmm256", choices=sorted(inputs.WORKLOADS) + ["batch32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
+    ap.add_argument("--kernel", choices=["kb", "gauss"], default="kb",
+                    help="interpolation kernel of G: Kaiser-Bessel or the paper's Gaussian")
     ap.add_argument("--precision", choices=["c64", "bf16"], default="c64",
                     help="storage of the measured visibilities y (bf16 pairs with per-4096 scales)")
     return ap.parse_args()
@@ -66,13 +68,13 @@ def workload_config(w: inputs.Workload) -> dict:
 # ---------------------------------------------------------------------------
 # FP64 CPU oracle: the reported baseline (and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None):
+def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None, kernel: str = "kb"):
     """SDMM iterations/s of the FP64 oracle on a bounded sample of the workload."""
     from oracle import sdmm as osdmm, simulate
 
     p = inputs.make_problem(w)
-    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db)
-    ops = simulate.operators(p.uv, w.n, w.J)
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db, kernel=kernel)
+    ops = simulate.operators(p.uv, w.n, w.J, kernel=kernel)
     st = osdmm.init_state(ops, y, (w.n, w.n))
     wts = np.ones((9, w.n, w.n))
     osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)  # the first iteration is trivial (x_hat = 0)
@@ -86,8 +88,8 @@ def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = Non
     return done / el, done, el
 
 
-def cpu_baseline_entry(w, budget_s, max_iters=None) -> dict:
-    rate, done, el = oracle_rate(w, budget_s, max_iters)
+def cpu_baseline_entry(w, budget_s, max_iters=None, kernel: str = "kb") -> dict:
+    rate, done, el = oracle_rate(w, budget_s, max_iters, kernel)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} SDMM iterations (after one untimed) of the {w.name} workload, FP64 numpy "
                       f"oracle, single thread, {el:.1f} s; host has {os.cpu_count()} cores"}
@@ -99,12 +101,12 @@ def run_reference(args, w):
         return
     # bounded: about a minute of oracle work whatever --steps is
     budget = min(60.0, max(10.0, 0.2 * (args.steps + args.warmup)))
-    entry = cpu_baseline_entry(w, budget)
+    entry = cpu_baseline_entry(w, budget, kernel=args.kernel)
     out = {"impl": "reference", "metric": METRIC, "value": entry["value"], "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 / entry["value"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(w),
+           "config": {**workload_config(w), "kernel": args.kernel},
            "cpu_baseline": entry,
            "e2e": {"value": entry["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -260,13 +262,13 @@ def run_gpu(args, w):
 
     cpu_entry = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds)
+        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds, kernel=args.kernel)
 
     # each rank: its own independent problem of the same shape
     p = inputs.make_problem(rank_workload(w, rank))
     from paper_1307_4370_gb300 import autotune
     tune = autotune.autotune_tile(w.n, p.uv, w.J, reps=10)  # grid-tile schedule, measured and cached
-    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J, tile=tune["tile"])
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J, tile=tune["tile"], kernel=args.kernel)
     x_true = torch.tensor(p.x_true.astype(np.complex64), device=dev)
     y0 = ctx.phi(x_true)
     sig = float(torch.linalg.vector_norm(y0).item()) / math.sqrt(w.M) * 10 ** (-w.isnr_db / 20)
@@ -382,7 +384,7 @@ def run_gpu(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**workload_config(w), "y_storage": args.precision,
+            "config": {**workload_config(w), "kernel": args.kernel, "y_storage": args.precision,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "cuda_graph": True, "tile": tune["tile"], "tile_ms": tune["timings"],
                        "parallelism": f"{world} independent problems (one per GPU)"},

@@ -77,6 +77,14 @@ typedef enum {
 } purify_status;
 
 /* Visibility storage formats of the measured data y (SDMM data only). */
+/* Interpolation kernel of G (§5): Kaiser-Bessel, or the paper's Gaussian
+ * g(t) = exp(-b t^2), b = pi (alpha - 1/2) / (alpha J / 2) with alpha = 2,
+ * D dividing by the transform of the untruncated Gaussian. */
+typedef enum {
+  PURIFY_KERNEL_KB = 0,
+  PURIFY_KERNEL_GAUSS = 1
+} purify_kernel;
+
 typedef enum {
   PURIFY_VIS_C64 = 0,       /* complex64 */
   PURIFY_VIS_BF16_BLOCK = 1 /* bf16 (re, im) pairs, one float32 scale per 4096 */
@@ -86,7 +94,7 @@ typedef enum {
  *   n           image side; N = n*n; a multiple of 2^levels; 2n must factor
  *               as 2^a 3^b with b <= 1; 8 <= n <= 2048.
  *   M           number of visibilities, 1 <= M <= 2^31 - 1.
- *   J           Kaiser-Bessel support per axis: 2, 4, 6 or 8.
+ *   J           kernel support per axis: 2, 4, 6 or 8.
  *   oversample  must be 2 (§6 uses k = 2; the grid is 2n x 2n).
  *   levels      wavelet levels of each Daubechies basis, 1..6 (4 in §6).
  *   bases_mask  bit 0 Dirac, bit p db_p (p = 1..8); SARA is 0x1FF.
@@ -94,7 +102,9 @@ typedef enum {
  *               choice, not part of the method): 0 picks a default from the
  *               grid size; otherwise 8, 16, 32 or 64, at least J and dividing
  *               2n.  The autotuner of the Python package measures the
- *               candidates.  */
+ *               candidates.
+ *   kernel      a purify_kernel (0, the zero-initialised default, is
+ *               Kaiser-Bessel).  */
 typedef struct {
   int32_t n;
   int64_t M;
@@ -103,6 +113,7 @@ typedef struct {
   int32_t levels;
   uint32_t bases_mask;
   int32_t tile;
+  int32_t kernel;
 } purify_desc;
 
 /* Create a context for one u-v coverage (§5: G depends only on the
@@ -125,11 +136,22 @@ const char* purify_status_string(int status);
  * string. */
 const char* purify_last_error(void);
 
+/* Primary beam B of Phi = G F D Z B (§5 eq. opmodel): a real n x n map
+ * (N float32, row-major like the image; host or device pointer), copied
+ * into the context during the call; NULL restores B = I (every experiment
+ * of §6).  Every later Phi, Phi^H, CG and SDMM call of this context applies
+ * it; SDMM states re-capture their iteration graph on their next step.  Do
+ * not call it while work of this context is in flight on other streams.  A
+ * batch (purify_batch_create) keeps the beam its graphs were built with:
+ * set the beam before creating the batch.  Synchronises `stream`.
+ * PURIFY_E_INVALID_ARG for a null context. */
+int purify_set_beam(purify_ctx* ctx, const float* beam, purify_stream_t stream);
+
 /* Sizes of a context: N = n*n, M, q = number of bases, D = q*N. */
 int purify_sizes(const purify_ctx* ctx, int64_t* N, int64_t* M, int32_t* q,
                  int64_t* D);
 
-/* y = Phi x (§5 eq. opmodel with B = I): x is N complex64 (device), y is M
+/* y = Phi x (§5 eq. opmodel; B = I unless purify_set_beam gave one): x is N complex64 (device), y is M
  * complex64 (device), visibilities in the order of the uv array given to
  * purify_create. */
 int purify_phi(purify_ctx* ctx, const float* x, float* y, purify_stream_t stream);

@@ -1,4 +1,4 @@
-"""Measurement operator Phi = G F D Z (B = I) and its adjoint (oracle).
+"""Measurement operator Phi = G F D Z B and its adjoint (oracle).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
@@ -18,7 +18,10 @@ Conventions (the paper fixes none of them; these are this build's reading):
 * F is X[k] = (1/(2n)) sum_j g[j] exp(-2 pi i k.j / (2n)), natural order;
 * G: kappa = u 2n / (2 pi); the footprint of a visibility is the J cells
   floor(kappa) - J/2 + 1 .. floor(kappa) + J/2 of each axis (indices mod
-  2n) weighted by g(kappa - k) of ``kaiser_bessel``.
+  2n) weighted by g(kappa - k) of ``kaiser_bessel`` (Kaiser-Bessel by
+  default, or the paper's Gaussian with ``kernel="gauss"``);
+* B: an optional real n x n primary beam multiplying the image (default the
+  identity, as in all of §6).
 
 ``phi_adj`` is the exact transpose-conjugate of each factor in reverse
 order: Z^T D F^H G^T.
@@ -31,7 +34,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from .kaiser_bessel import OVERSAMPLE, deapodisation, kb_kernel
+from .kaiser_bessel import OVERSAMPLE, deapodisation
+from .kaiser_bessel import kernel as interp_kernel
 
 
 def _pad_rows(n: int) -> np.ndarray:
@@ -47,20 +51,20 @@ def footprint(uv: np.ndarray, n: int, J: int):
     return k0, kappa
 
 
-def zero_pad_deapodise(x: np.ndarray, J: int) -> np.ndarray:
+def zero_pad_deapodise(x: np.ndarray, J: int, kernel: str = "kb") -> np.ndarray:
     """D Z x: the image divided by g_hat, placed on the 2n x 2n grid."""
     n = x.shape[0]
     L = OVERSAMPLE * n
-    gh = deapodisation(n, J)
+    gh = deapodisation(n, J, kernel)
     g = np.zeros((L, L), dtype=np.complex128)
     rows = _pad_rows(n)
     g[np.ix_(rows, rows)] = x / np.outer(gh, gh)
     return g
 
 
-def crop_deapodise(g: np.ndarray, n: int, J: int) -> np.ndarray:
+def crop_deapodise(g: np.ndarray, n: int, J: int, kernel: str = "kb") -> np.ndarray:
     """Z^T D g: the image pixels of a grid, divided by g_hat."""
-    gh = deapodisation(n, J)
+    gh = deapodisation(n, J, kernel)
     rows = _pad_rows(n)
     return g[np.ix_(rows, rows)] / np.outer(gh, gh)
 
@@ -75,16 +79,16 @@ def ifft2_unitary(X: np.ndarray) -> np.ndarray:
     return np.fft.ifft2(X) * np.sqrt(X.size)
 
 
-def _axis_weights(k0: np.ndarray, kappa: np.ndarray, J: int):
+def _axis_weights(k0: np.ndarray, kappa: np.ndarray, J: int, kernel: str = "kb"):
     """Per-axis kernel weights g(kappa - k0 - a), a = 0..J-1, as J arrays of (M, 2)."""
-    return [kb_kernel(kappa - (k0 + a), J) for a in range(J)]
+    return [interp_kernel(kappa - (k0 + a), J, kernel) for a in range(J)]
 
 
-def degrid(X: np.ndarray, uv: np.ndarray, J: int) -> np.ndarray:
+def degrid(X: np.ndarray, uv: np.ndarray, J: int, kernel: str = "kb") -> np.ndarray:
     """G: y_m = sum_{a,b < J} g(kappa_m0 - k0_m0 - a) g(kappa_m1 - k0_m1 - b) X[k0 + (a, b)]."""
     L = X.shape[0]
     k0, kappa = footprint(uv, L // OVERSAMPLE, J)
-    w = _axis_weights(k0, kappa, J)
+    w = _axis_weights(k0, kappa, J, kernel)
     y = np.zeros(k0.shape[0], dtype=np.complex128)
     for a in range(J):
         k_r = (k0[:, 0] + a) % L
@@ -94,11 +98,11 @@ def degrid(X: np.ndarray, uv: np.ndarray, J: int) -> np.ndarray:
     return y
 
 
-def grid(y: np.ndarray, uv: np.ndarray, n: int, J: int) -> np.ndarray:
+def grid(y: np.ndarray, uv: np.ndarray, n: int, J: int, kernel: str = "kb") -> np.ndarray:
     """G^T: X[k] = sum_m g(kappa_m0 - k0) g(kappa_m1 - k1) y_m (G is real)."""
     L = OVERSAMPLE * n
     k0, kappa = footprint(uv, n, J)
-    w = _axis_weights(k0, kappa, J)
+    w = _axis_weights(k0, kappa, J, kernel)
     y = np.asarray(y, dtype=np.complex128)
     X = np.zeros(L * L, dtype=np.complex128)
     for a in range(J):
@@ -112,17 +116,20 @@ def grid(y: np.ndarray, uv: np.ndarray, n: int, J: int) -> np.ndarray:
     return X.reshape(L, L)
 
 
-def phi(x: np.ndarray, uv: np.ndarray, J: int) -> np.ndarray:
-    """Phi x = G F D Z x for an n x n image x and M frequencies uv."""
-    return degrid(fft2_unitary(zero_pad_deapodise(x, J)), uv, J)
+def phi(x: np.ndarray, uv: np.ndarray, J: int, kernel: str = "kb", beam: np.ndarray | None = None) -> np.ndarray:
+    """Phi x = G F D Z B x for an n x n image x and M frequencies uv."""
+    bx = x if beam is None else np.asarray(beam, dtype=np.float64) * x
+    return degrid(fft2_unitary(zero_pad_deapodise(bx, J, kernel)), uv, J, kernel)
 
 
-def phi_adj(y: np.ndarray, uv: np.ndarray, n: int, J: int) -> np.ndarray:
-    """Phi^H y = Z^T D F^H G^T y, an n x n image."""
-    return crop_deapodise(ifft2_unitary(grid(y, uv, n, J)), n, J)
+def phi_adj(y: np.ndarray, uv: np.ndarray, n: int, J: int, kernel: str = "kb",
+            beam: np.ndarray | None = None) -> np.ndarray:
+    """Phi^H y = B Z^T D F^H G^T y, an n x n image (B is real and diagonal)."""
+    x = crop_deapodise(ifft2_unitary(grid(y, uv, n, J, kernel)), n, J, kernel)
+    return x if beam is None else np.asarray(beam, dtype=np.float64) * x
 
 
-def nudft(x: np.ndarray, uv: np.ndarray) -> np.ndarray:
+def nudft(x: np.ndarray, uv: np.ndarray, beam: np.ndarray | None = None) -> np.ndarray:
     """Direct non-uniform DFT, (1/(2n)) sum_l x_l exp(-i u.l).
 
     This is the quantity Phi approximates (eq. ri1 without DDEs, sampled on
@@ -130,6 +137,8 @@ def nudft(x: np.ndarray, uv: np.ndarray) -> np.ndarray:
     oversampled grid.  O(M N): for small inputs only.
     """
     n = x.shape[0]
+    if beam is not None:
+        x = np.asarray(beam, dtype=np.float64) * x
     l = np.arange(n) - n // 2
     uv = np.asarray(uv, dtype=np.float64)
     e0 = np.exp(-1j * np.outer(uv[:, 0], l))  # (M, n)

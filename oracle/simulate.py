@@ -33,19 +33,20 @@ def snr_db(x: np.ndarray, x_hat: np.ndarray) -> float:
 
 
 def visibilities(x_true: np.ndarray, uv: np.ndarray, J: int, noise_unit: np.ndarray,
-                 isnr_db: float) -> tuple[np.ndarray, float]:
+                 isnr_db: float, kernel: str = "kb", beam=None) -> tuple[np.ndarray, float]:
     """y = Phi x + n and eps, with n = sigma_n * noise_unit."""
-    y0 = measurement.phi(x_true.astype(np.complex128), uv, J)
+    y0 = measurement.phi(x_true.astype(np.complex128), uv, J, kernel, beam)
     sig = noise_sigma(y0, isnr_db)
     return y0 + sig * noise_unit, l2_bound(y0.size, sig)
 
 
 def operators(uv: np.ndarray, n: int, J: int, levels: int = 4,
-              bases=sara.ALL_BASES) -> sdmm.Operators:
-    """The operators of eq. cvx2 for one problem."""
+              bases=sara.ALL_BASES, kernel: str = "kb", beam=None) -> sdmm.Operators:
+    """The operators of eq. cvx2 for one problem (interpolation kernel and
+    primary beam of Phi = G F D Z B selectable)."""
     return sdmm.Operators(
-        phi=lambda x: measurement.phi(x, uv, J),
-        phi_adj=lambda y: measurement.phi_adj(y, uv, n, J),
+        phi=lambda x: measurement.phi(x, uv, J, kernel, beam),
+        phi_adj=lambda y: measurement.phi_adj(y, uv, n, J, kernel, beam),
         psi_adj=lambda x: sara.sara_analysis(x, levels, bases),
         psi=lambda a: sara.sara_synthesis(a, levels, bases),
     )

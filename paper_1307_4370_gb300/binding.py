@@ -41,7 +41,10 @@ class PurifyError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("M", ctypes.c_int64), ("J", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("levels", ctypes.c_int32), ("bases_mask", ctypes.c_uint32),
-                ("tile", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
+KERNELS = {"kb": 0, "gauss": 1}  # purify_kernel: Kaiser-Bessel, the paper's Gaussian
 
 
 class SdmmParams(ctypes.Structure):
@@ -66,6 +69,7 @@ _SIGS = {
     "purify_destroy": (None, [_vp]),
     "purify_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "purify_last_error": (ctypes.c_char_p, []),
+    "purify_set_beam": (_i32, [_vp, _vp, _vp]),
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -183,7 +187,7 @@ class Context:
     """
 
     def __init__(self, n: int, uv, J: int = 6, levels: int = 4, bases_mask: int = SARA_MASK,
-                 device=None, tile: int = 0):
+                 device=None, tile: int = 0, kernel: str = "kb"):
         self.lib = load()
         if device is not None:
             torch.cuda.set_device(device)
@@ -201,9 +205,23 @@ class Context:
         self.N = self.n * self.n
         self.D = self.q * self.N
         self.tile = int(tile)
-        desc = Desc(self.n, self.M, self.J, 2, self.levels, self.bases_mask, self.tile)
+        if kernel not in KERNELS:
+            raise ValueError(f"kernel must be one of {sorted(KERNELS)}")
+        self.kernel = kernel
+        desc = Desc(self.n, self.M, self.J, 2, self.levels, self.bases_mask, self.tile, KERNELS[kernel])
         uv_keep = uv_t if uv_t.is_cuda else uv_t.numpy()
         self.ctx = purify_create(desc, _ptr(uv_keep))
+
+    def set_beam(self, beam=None, stream=None) -> None:
+        """Primary beam B of Phi = G F D Z B: a real n x n map, or None for B = I."""
+        if beam is None:
+            _check("purify_set_beam", self.lib.purify_set_beam(self.ctx, None, _stream(stream)))
+            return
+        b = torch.as_tensor(beam, dtype=torch.float32)
+        if tuple(b.shape) not in ((self.n, self.n), (self.N,)):
+            raise ValueError("beam must be n x n")
+        b = b.to(self.device).contiguous()
+        _check("purify_set_beam", self.lib.purify_set_beam(self.ctx, _ptr(b), _stream(stream)))
 
     def close(self) -> None:
         if getattr(self, "ctx", None):

@@ -115,10 +115,28 @@ void solve_dense(std::vector<long double>& A, std::vector<long double>& b, int n
   }
 }
 
+// The paper's Gaussian kernel (§5): g(t) = exp(-b t^2) on |t| <= J/2 with
+// b = pi (alpha - 1/2) / (alpha J / 2), alpha = 2 (the width of Greengard &
+// Lee 2004 in grid cells); g_hat is the transform of the untruncated Gaussian.
+double gauss_b(int J) { return M_PI * 1.5 / (2.0 * (J / 2.0)); }
+double gauss_g(double t, int J) { return std::fabs(t) <= J / 2.0 ? std::exp(-gauss_b(J) * t * t) : 0.0; }
+double gauss_ghat(double f, int J) {
+  const double b = gauss_b(J);
+  return std::sqrt(M_PI / b) * std::exp(-M_PI * M_PI * f * f / b);
+}
+
+// g and g_hat of the context's kernel.
+double interp_g(double t, int J, int kernel, double beta, double i0b) {
+  return kernel == PURIFY_KERNEL_GAUSS ? gauss_g(t, J) : kb_g(t, J, beta, i0b);
+}
+double interp_ghat(double f, int J, int kernel, double beta, double i0b) {
+  return kernel == PURIFY_KERNEL_GAUSS ? gauss_ghat(f, J) : kb_ghat(f, J, beta, i0b);
+}
+
 // Fit each tap's weight, as a function of z = 2x - 1 on [-1, 1], by the
 // degree-kKbDeg polynomial interpolating it at Chebyshev nodes (long double),
 // and record the largest error of its float Horner evaluation.
-KbPoly fit_kb(int J) {
+KbPoly fit_kb(int J, int kernel) {
   const double beta = kb_beta(J);
   const double i0b = std::cyl_bessel_i(0.0, beta);
   KbPoly kb{};
@@ -135,7 +153,7 @@ KbPoly fit_kb(int J) {
         A[i * np + j] = zp;
         zp *= z;
       }
-      f[i] = kb_g(x + J / 2 - 1 - a, J, beta, i0b);
+      f[i] = interp_g(x + J / 2 - 1 - a, J, kernel, beta, i0b);
     }
     solve_dense(A, f, np);
     for (int j = 0; j < np; ++j) kb.c[a][j] = (float)f[j];
@@ -144,7 +162,7 @@ KbPoly fit_kb(int J) {
       const float z = std::fma(2.0f, (float)x, -1.0f);
       float acc = kb.c[a][kKbDeg];
       for (int k = kKbDeg - 1; k >= 0; --k) acc = std::fma(acc, z, kb.c[a][k]);
-      err = std::max(err, (float)std::fabs(acc - kb_g(x + J / 2 - 1 - a, J, beta, i0b)));
+      err = std::max(err, (float)std::fabs(acc - interp_g(x + J / 2 - 1 - a, J, kernel, beta, i0b)));
     }
   }
   kb.max_err = err;
@@ -228,7 +246,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -519,6 +537,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   if (d->n < 8 || d->n > 2048 || d->n % (1 << d->levels) != 0 || d->n % 2 != 0) return PURIFY_E_SIZE;
   if (d->M < 1 || d->M > 2147483647LL) return PURIFY_E_SIZE;
   if (d->bases_mask == 0 || (d->bases_mask & ~0x1FFu)) return PURIFY_E_INVALID_ARG;
+  if (d->kernel != PURIFY_KERNEL_KB && d->kernel != PURIFY_KERNEL_GAUSS) return PURIFY_E_INVALID_ARG;
   if (!good_side(2 * d->n)) return PURIFY_E_UNSUPPORTED;
   if (d->tile != 0 && ((d->tile != 8 && d->tile != 16 && d->tile != 32 && d->tile != 64) || d->tile < d->J ||
                        (2 * d->n) % d->tile != 0))
@@ -530,13 +549,14 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   c->n = d->n;
   c->L = 2 * d->n;
   c->J = d->J;
+  c->kernel = d->kernel;
   c->levels = d->levels;
   c->M = d->M;
   c->mask = d->bases_mask;
   c->q = 0;
   for (int b = 0; b < 9; ++b)
     if (c->mask & (1u << b)) c->bases[c->q++] = b;
-  c->kb = fit_kb(c->J);
+  c->kb = fit_kb(c->J, c->kernel);
   const double sc = (double)c->L / (2.0 * M_PI);
   c->ks.hi = (float)sc;
   c->ks.lo = (float)(sc - (double)c->ks.hi);
@@ -568,7 +588,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   {
     const double beta = kb_beta(c->J), i0b = std::cyl_bessel_i(0.0, beta);
     std::vector<float> dz(c->n);
-    for (int r = 0; r < c->n; ++r) dz[r] = (float)(1.0 / kb_ghat((double)(r - c->n / 2) / c->L, c->J, beta, i0b));
+    for (int r = 0; r < c->n; ++r) dz[r] = (float)(1.0 / interp_ghat((double)(r - c->n / 2) / c->L, c->J, c->kernel, beta, i0b));
     std::vector<float2> tw(c->L);
     for (int m = 0; m < c->L; ++m) {
       const double a = -2.0 * M_PI * (double)m / c->L;
@@ -594,6 +614,22 @@ void purify_destroy(purify_ctx* c) {
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
   free_ctx(c);
+}
+
+int purify_set_beam(purify_ctx* c, const float* beam, purify_stream_t stream) {
+  if (!c) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!beam) {
+    c->beam_on = false;  // the buffer stays until purify_destroy
+  } else {
+    if (!c->d_beam) TRY(dev_alloc(&c->d_beam, ctx_N(c)));
+    TRY_CUDA(cudaMemcpyAsync(c->d_beam, beam, ctx_N(c) * sizeof(float), cudaMemcpyDefault, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    c->beam_on = true;
+  }
+  c->beam_version++;
+  return PURIFY_OK;
 }
 
 int purify_sizes(const purify_ctx* c, int64_t* N, int64_t* M, int32_t* q, int64_t* D) {
@@ -828,7 +864,7 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
     TRY(enqueue_sdmm_step(c, st, s));
   } else {
     const int key = st->params.cg_iters * 2 + st->y_bf16;
-    if (!st->step_exec || st->graph_cg_iters != key) {
+    if (!st->step_exec || st->graph_cg_iters != key || st->graph_beam != c->beam_version) {
       TRY(drop_graph(st));
       if (!st->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
       TRY_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -847,6 +883,7 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
         return PURIFY_E_CUDA;
       }
       st->graph_cg_iters = key;
+      st->graph_beam = c->beam_version;
       g_launches.fetch_sub((unsigned long long)st->launches_per_step, std::memory_order_relaxed);  // capture only
     }
     TRY_CUDA(cudaGraphLaunch(st->step_exec, s));

@@ -222,6 +222,10 @@ constexpr size_t kGridSmemBudget = 72 * 1024;
 struct purify_ctx {
   int device;
   int n, L, J, levels, q;
+  int kernel;           // PURIFY_KERNEL_KB or PURIFY_KERNEL_GAUSS
+  float* d_beam;        // primary beam B (N floats), allocated by the first purify_set_beam
+  bool beam_on;         // B applied (otherwise B = I)
+  int beam_version;     // bumped by every purify_set_beam (graphs re-capture)
   int64_t M;
   uint32_t mask;
   int bases[9];  // basis index (0 = Dirac, p = db_p) of each plane
@@ -334,6 +338,7 @@ struct purify_sdmm_state {
   cudaStream_t cap_stream;
   cudaGraphExec_t step_exec;
   int graph_cg_iters;       // key of the captured graph (cg_iters, data format)
+  int graph_beam;           // beam version of the context when it was captured
   int launches_per_step;    // kernels in one captured step
 };
 

@@ -86,6 +86,7 @@ struct RowFwdSrc {
   using Raw = typename std::conditional<MODE == kRowInPlain, RawPlain, RawCg>::type;
   RowInArgs a;
   const float* dz;
+  const float* beam;  // primary beam B (N), or null
   int n, L, r0;
   float invL, alpha, beta;
   bool first;
@@ -98,6 +99,7 @@ struct RowFwdSrc {
     if (cc < n) {
       o.off = row * n + cc;
       o.f = __ldg(&dz[row]) * __ldg(&dz[cc]) * invL;
+      if (beam) o.f *= __ldg(&beam[o.off]);
       if constexpr (MODE == kRowInPlain) {
         o.v = a.in[o.off];
       } else {
@@ -143,13 +145,14 @@ struct RowStoreDst {  // row-major rows of length L
 
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(256) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
-                                                 const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
-                                                 const DevScalars* __restrict__ sc) {
+                                                 const float* __restrict__ beam, const float2* __restrict__ tw,
+                                                 FftPlan plan, int n, int nsig, const DevScalars* __restrict__ sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
   RowFwdSrc<MODE> src;
   src.a = a;
   src.dz = dz;
+  src.beam = beam;
   src.n = n;
   src.L = L;
   src.r0 = blockIdx.x * nsig;
@@ -736,6 +739,7 @@ struct RowInvDst {
   using Aux = AuxPix;
   RowOutArgs a;
   const float* dz;
+  const float* beam;  // primary beam B (N), or null
   int n, L, r0;
   float invL;
   FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
@@ -748,6 +752,7 @@ struct RowInvDst {
     if (c < n) {
       o.off = row * n + c;
       o.f = __ldg(&dz[row]) * __ldg(&dz[c]) * invL;
+      if (beam) o.f *= __ldg(&beam[o.off]);
       if (MODE != kRowOutPlain) o.p = a.p[o.off];
       if (MODE == kRowOutSdmm) {
         o.z3 = a.z3[o.off];
@@ -786,8 +791,9 @@ struct RowInvDst {
 
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half, RowOutArgs a,
-                                                 const float* __restrict__ dz, const float2* __restrict__ tw,
-                                                 FftPlan plan, int n, int nsig, double* partials, DevScalars* sc) {
+                                                 const float* __restrict__ dz, const float* __restrict__ beam,
+                                                 const float2* __restrict__ tw, FftPlan plan, int n, int nsig,
+                                                 double* partials, DevScalars* sc) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
   const int r0 = blockIdx.x * nsig;
@@ -795,6 +801,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half
   RowInvDst<MODE> dst;
   dst.a = a;
   dst.dz = dz;
+  dst.beam = beam;
   dst.n = n;
   dst.L = L;
   dst.r0 = r0;
@@ -825,6 +832,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half
 // Host launchers
 // ---------------------------------------------------------------------------
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s) {
+  const float* beam = c->beam_on ? c->d_beam : nullptr;
   const FftShape rs = row_shape(c), cs = col_shape(c);
   const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
   const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);
@@ -833,7 +841,7 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
   do {                                                                                                     \
     allow_smem(k_row_fwd<E, MD>, smr);                                                                     \
     PURIFY_LAUNCH(c, "row_fwd", s,                                                                         \
-                  (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, c->d_tw, c->plan,  \
+                  (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, beam, c->d_tw, c->plan, \
                                                                 c->n, rs.nsig, c->d_sc)));                   \
   } while (0)
   if (rs.ept == 8) {
@@ -927,6 +935,7 @@ int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) 
 }
 
 int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* grid) {
+  const float* beam = c->beam_on ? c->d_beam : nullptr;
   const float2* Xg = grid ? grid : c->d_grid;
   const FftShape rs = row_shape(c), cs = col_shape(c);
   const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
@@ -945,7 +954,7 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
   do {                                                                                                       \
     allow_smem(k_row_inv<E, MD>, smr);                                                                       \
     PURIFY_LAUNCH(c, "row_inv", s,                                                                           \
-                  (k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, c->d_tw, c->plan,  \
+                  (k_row_inv<E, MD><<<gr, rs.threads, smr, s>>>(c->d_half, a, c->d_deapod, beam, c->d_tw, c->plan, \
                                                                 c->n, rs.nsig, c->d_partials, c->d_sc)));     \
   } while (0)
   if (rs.ept == 8) {

@@ -56,7 +56,7 @@ def test_default_params(lib):
     ("n", 7, -2), ("n", 20, -2), ("n", 4096 * 2, -2), ("J", 5, -2), ("J", 10, -2),
     ("oversample", 3, -2), ("levels", 0, -2), ("levels", 7, -2), ("M", 0, -2),
     ("bases_mask", 0, -1), ("bases_mask", 0x200, -1), ("n", 80, -7),
-    ("tile", 12, -2), ("tile", 2, -2), ("tile", 128, -2),
+    ("tile", 12, -2), ("tile", 2, -2), ("tile", 128, -2), ("kernel", 2, -1), ("kernel", -1, -1),
 ])
 def test_create_rejects_bad_descriptions(lib, field, value, code):
     from paper_1307_4370_gb300 import binding
@@ -81,5 +81,6 @@ def test_null_arguments(lib):
     assert lib.purify_create(ctypes.byref(out), None, None, None) == -1
     assert lib.purify_phi(None, None, None, None) == -1
     assert lib.purify_sdmm_step(None, None, None) == -1
+    assert lib.purify_set_beam(None, None, None) == -1
     lib.purify_destroy(None)
     lib.purify_sdmm_state_destroy(None)

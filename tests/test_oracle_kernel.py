@@ -69,3 +69,38 @@ def test_deapodisation_profile():
     gh = kb.deapodisation(n, 6)
     assert np.argmax(gh) == n // 2
     assert np.allclose(gh[1:], gh[1:][::-1], rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# The paper's Gaussian kernel (§5)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("J", [4, 6, 8])
+@pytest.mark.parametrize("f", [0.0, 0.05, 0.125, 0.25])
+def test_gauss_transform_matches_quadrature(J, f):
+    # g_hat is the transform of the untruncated Gaussian: integrate over R.
+    b = kb.gauss_b(J)
+    val, _ = integrate.quad(lambda t: np.exp(-b * t * t) * np.cos(2 * np.pi * f * t), -np.inf, np.inf,
+                            epsabs=1e-15, epsrel=1e-14, limit=400)
+    assert abs(kb.gauss_transform(f, J) - val) <= 1e-12 * abs(val)
+
+
+@pytest.mark.parametrize("J", [4, 6, 8])
+def test_gauss_kernel_shape(J):
+    # exp(-b t^2) with b = pi (alpha - 1/2) / (alpha J / 2): 1 at the centre,
+    # exp(-3 pi J / 8) at the support edge (alpha = 2), zero outside, even.
+    assert kb.gauss_b(J) == pytest.approx(0.75 * np.pi / (J / 2), rel=1e-15)
+    assert kb.gauss_kernel(0.0, J) == 1.0
+    assert kb.gauss_kernel(J / 2, J) == pytest.approx(np.exp(-3 * np.pi * J / 8), rel=1e-14)
+    assert kb.gauss_kernel(J / 2 + 1e-9, J) == 0.0
+    t = np.linspace(-J / 2, J / 2, 101)
+    assert np.array_equal(kb.gauss_kernel(t, J), kb.gauss_kernel(-t, J))
+    assert np.array_equal(kb.kernel(t, J, "gauss"), kb.gauss_kernel(t, J))
+    assert np.array_equal(kb.kernel(t, J, "kb"), kb.kb_kernel(t, J))
+
+
+def test_gauss_deapodisation_profile():
+    n = 64
+    gh = kb.deapodisation(n, 6, "gauss")
+    l = np.arange(n) - n // 2
+    assert np.allclose(gh, kb.gauss_transform(l / (2 * n), 6), rtol=1e-15, atol=0)
+    assert np.argmax(gh) == n // 2
