@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--kernel", choices=["kb", "gauss"], default="kb",
                     help="interpolation kernel of G: Kaiser-Bessel or the paper's Gaussian")
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="distributed-block form (one l2 ball per block of equal size); 0 = one ball")
     ap.add_argument("--precision", choices=["c64", "bf16"], default="c64",
                     help="storage of the measured visibilities y (bf16 pairs with per-4096 scales)")
     return ap.parse_args()
@@ -68,19 +70,39 @@ def workload_config(w: inputs.Workload) -> dict:
 # ---------------------------------------------------------------------------
 # FP64 CPU oracle: the reported baseline (and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None, kernel: str = "kb"):
+def block_table(M: int, R: int, eps: float):
+    """R equal consecutive blocks and their chi^2 bounds (sigma_n recovered from eps)."""
+    from oracle import simulate
+
+    offsets = [M * i // R for i in range(R + 1)]
+    sig = eps / math.sqrt(M + 2 * math.sqrt(M))
+    return offsets, [simulate.l2_bound(offsets[i + 1] - offsets[i], sig) for i in range(R)]
+
+
+def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None, kernel: str = "kb",
+                blocks: int = 0):
     """SDMM iterations/s of the FP64 oracle on a bounded sample of the workload."""
     from oracle import sdmm as osdmm, simulate
 
     p = inputs.make_problem(w)
     y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db, kernel=kernel)
     ops = simulate.operators(p.uv, w.n, w.J, kernel=kernel)
-    st = osdmm.init_state(ops, y, (w.n, w.n))
     wts = np.ones((9, w.n, w.n))
-    osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)  # the first iteration is trivial (x_hat = 0)
+    if blocks > 0:
+        offsets, eps_b = block_table(w.M, blocks, eps)
+        st = osdmm.init_state_blocks(ops, y, offsets, (w.n, w.n))
+
+        def iteration():
+            osdmm.sdmm_iteration_blocks(ops, st, y, eps_b, offsets, wts, w.cg_iters)
+    else:
+        st = osdmm.init_state(ops, y, (w.n, w.n))
+
+        def iteration():
+            osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)
+    iteration()  # the first iteration is trivial (x_hat = 0)
     done, t0 = 0, time.perf_counter()
     while True:
-        osdmm.sdmm_iteration(ops, st, y, eps, wts, w.cg_iters)
+        iteration()
         done += 1
         el = time.perf_counter() - t0
         if el >= budget_s or (max_iters is not None and done >= max_iters):
@@ -88,8 +110,8 @@ def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = Non
     return done / el, done, el
 
 
-def cpu_baseline_entry(w, budget_s, max_iters=None, kernel: str = "kb") -> dict:
-    rate, done, el = oracle_rate(w, budget_s, max_iters, kernel)
+def cpu_baseline_entry(w, budget_s, max_iters=None, kernel: str = "kb", blocks: int = 0) -> dict:
+    rate, done, el = oracle_rate(w, budget_s, max_iters, kernel, blocks)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} SDMM iterations (after one untimed) of the {w.name} workload, FP64 numpy "
                       f"oracle, single thread, {el:.1f} s; host has {os.cpu_count()} cores"}
@@ -101,12 +123,12 @@ def run_reference(args, w):
         return
     # bounded: about a minute of oracle work whatever --steps is
     budget = min(60.0, max(10.0, 0.2 * (args.steps + args.warmup)))
-    entry = cpu_baseline_entry(w, budget, kernel=args.kernel)
+    entry = cpu_baseline_entry(w, budget, kernel=args.kernel, blocks=args.blocks)
     out = {"impl": "reference", "metric": METRIC, "value": entry["value"], "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 / entry["value"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {**workload_config(w), "kernel": args.kernel},
+           "config": {**workload_config(w), "kernel": args.kernel, "blocks": args.blocks},
            "cpu_baseline": entry,
            "e2e": {"value": entry["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -262,7 +284,7 @@ def run_gpu(args, w):
 
     cpu_entry = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds, kernel=args.kernel)
+        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds, kernel=args.kernel, blocks=args.blocks)
 
     # each rank: its own independent problem of the same shape
     p = inputs.make_problem(rank_workload(w, rank))
@@ -277,6 +299,8 @@ def run_gpu(args, w):
     eps = binding.l2_bound(w.M, sig)
     st = ctx.sdmm_state()
     st.init(y, eps, cg_iters=w.cg_iters)
+    if args.blocks > 0:
+        st.set_blocks(*block_table(w.M, args.blocks, eps))
     if args.precision == "bf16":
         st.set_data_bf16(y)
     stream = torch.cuda.current_stream()
@@ -384,7 +408,8 @@ def run_gpu(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**workload_config(w), "kernel": args.kernel, "y_storage": args.precision,
+            "config": {**workload_config(w), "kernel": args.kernel, "blocks": args.blocks,
+                       "y_storage": args.precision,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "cuda_graph": True, "tile": tune["tile"], "tile_ms": tune["timings"],
                        "parallelism": f"{world} independent problems (one per GPU)"},

@@ -246,6 +246,8 @@ typedef struct {
   double nu;          /* ||y - Phi x_hat|| / eps */
   double gamma;       /* penalty parameter */
   double cg_residual; /* CG recurrence residual of the last x-update */
+  double nu_min;      /* distributed form: the smallest block's nu (nu is the
+                         largest); equal to nu for a single ball */
 } purify_report;
 
 /* Allocate the iteration variables of Algorithm 1 for a context. */
@@ -276,6 +278,24 @@ int purify_sdmm_set_data_bf16(purify_ctx* ctx, purify_sdmm_state* st, const floa
 
 /* One SDMM iteration (Algorithm 1 steps 5-9). */
 int purify_sdmm_step(purify_ctx* ctx, purify_sdmm_state* st, purify_stream_t stream);
+
+/* Distributed-block form (§4.5 eqs. blocks, dbp1, dbp2): the visibilities,
+ * in the caller's order, are cut into R consecutive blocks y_1 .. y_R with
+ * offsets[0] = 0 < offsets[1] < ... < offsets[R] = M (host array of R + 1),
+ * and block i must satisfy ||y_i - Phi_i x|| <= eps[i] (host array of R,
+ * all > 0) in place of the single ball of purify_sdmm_init.  SDMM then runs
+ * with S = R + 2 functions; Q = Phi^H Phi + 2I is unchanged, the data
+ * branch projects every block onto its own ball (factors and nu_i in FP64),
+ * and the report's nu / nu_min are the largest / smallest nu_i (the halting
+ * test of purify_sdmm_solve asks every nu_i to lie in the band).
+ * 1 <= R <= 4096; R = 0 (offsets, eps may be NULL) returns to the single
+ * ball.  The setting belongs to the state, survives purify_sdmm_init and
+ * is not part of purify_sdmm_export.  Synchronises `stream`.
+ * PURIFY_E_INVALID_ARG for offsets that are not increasing from 0 to M or a
+ * bound that is not positive. */
+int purify_sdmm_set_blocks(purify_ctx* ctx, purify_sdmm_state* st, int32_t R,
+                           const int64_t* offsets, const double* eps,
+                           purify_stream_t stream);
 
 /* Start a new reweighting round (§3.3): w_j = delta / (delta + |alpha_j|),
  * alpha = Psi^H x_hat, delta = max(10^-round ||alpha||_inf,

@@ -45,6 +45,17 @@ def project_l2_ball(r: np.ndarray, y: np.ndarray, eps: float) -> np.ndarray:
     return y + (eps / nd) * d
 
 
+def project_l2_balls(r: np.ndarray, y: np.ndarray, eps, offsets) -> np.ndarray:
+    """Block by block P_{B_i}, B_i = {r_i : ||r_i - y_i||_2 <= eps_i}: the data
+    constraints of the distributed form (§4.5 eq. dbp1), blocks
+    r[offsets[i]:offsets[i+1]] as in eq. blocks."""
+    out = np.empty(len(r), dtype=np.complex128)
+    for i in range(len(eps)):
+        sl = slice(offsets[i], offsets[i + 1])
+        out[sl] = project_l2_ball(r[sl], y[sl], eps[i])
+    return out
+
+
 def project_positive(a: np.ndarray) -> np.ndarray:
     """Projection onto {x real, x >= 0}: max(Re a, 0)."""
     return np.maximum(np.real(a), 0.0).astype(np.complex128)

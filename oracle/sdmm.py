@@ -163,3 +163,110 @@ def solve(ops: Operators, y: np.ndarray, eps: float, image_shape, coeff_shape,
                 break
     st.weights = w
     return st
+
+
+# ---------------------------------------------------------------------------
+# Distributed-block form (§4.5 eqs. blocks, dbp1, dbp2)
+# ---------------------------------------------------------------------------
+# y and Phi are cut into R row blocks y_i, Phi_i (eq. blocks), each with its
+# own bound eps_i (eq. dbp1).  Eq. dbp2 is Algorithm 1 with S = R + 2:
+# f1 = ||W .||_1 with L1 = Psi^H, f2 = positivity with L2 = I, and f_{i+2}
+# the indicator of the ball B_i with L_{i+2} = Phi_i.  Q = sum_i L_i^H L_i =
+# Psi Psi^H + I + sum_i Phi_i^H Phi_i = Phi^H Phi + 2I, the same as for one
+# ball.  Each block's x_{i+2} = Phi_i^H (r_{i+2} - z_{i+2}) is formed on its
+# own (Phi_i^H v_i is Phi^H of v_i placed in block i, zeros elsewhere).
+# Halting reading: every nu_i = ||y_i - Phi_i x_hat|| / eps_i in the band.
+
+
+@dataclasses.dataclass
+class BlockState:
+    """SDMM variables of eq. dbp2 after iteration ``t`` (per-block lists for f_{i+2})."""
+
+    x_hat: np.ndarray
+    z1: np.ndarray
+    x1: np.ndarray
+    z2: np.ndarray            # positivity (L2 = I)
+    x2: np.ndarray
+    zb: list                  # z_{i+2}, one array of M_i per block
+    xb: list                  # x_{i+2} = Phi_i^H (r_{i+2} - z_{i+2}), images
+    gamma: float
+    t: int = 0
+    f1_prev: float = 0.0
+    history: list = dataclasses.field(default_factory=list)
+
+
+def _block_adj(ops: Operators, v: np.ndarray, offsets, i: int, M: int) -> np.ndarray:
+    """Phi_i^H v for v in C^{M_i}."""
+    full = np.zeros(M, dtype=np.complex128)
+    full[offsets[i]:offsets[i + 1]] = v
+    return ops.phi_adj(full)
+
+
+def init_state_blocks(ops: Operators, y: np.ndarray, offsets, image_shape, beta: float = BETA) -> BlockState:
+    """Algorithm 1 steps 1-3 for eq. dbp2 with x_hat(0) = 0 (so every r_i(0), x_i(0) = 0)."""
+    x0 = np.zeros(image_shape, dtype=np.complex128)
+    R = len(offsets) - 1
+    M = int(offsets[-1])
+    z1 = np.zeros_like(ops.psi_adj(x0))
+    return BlockState(x_hat=x0, z1=z1, x1=ops.psi(z1), z2=x0.copy(), x2=x0.copy(),
+                      zb=[np.zeros(offsets[i + 1] - offsets[i], dtype=np.complex128) for i in range(R)],
+                      xb=[_block_adj(ops, np.zeros(offsets[i + 1] - offsets[i]), offsets, i, M)
+                          for i in range(R)],
+                      gamma=penalty(ops, y, beta))
+
+
+def sdmm_iteration_blocks(ops: Operators, st: BlockState, y: np.ndarray, eps, offsets, w: np.ndarray,
+                          cg_iters: int) -> dict:
+    """One pass of Algorithm 1 steps 5-9 for eq. dbp2; updates ``st`` in place."""
+    def apply_q(v):
+        return ops.phi_adj(ops.phi(v)) + 2.0 * v
+
+    R = len(eps)
+    M = int(offsets[-1])
+    # step 5
+    b = st.x1 + st.x2
+    for i in range(R):
+        b = b + st.xb[i]
+    st.x_hat, cg_res = cg_mod.cg(apply_q, b, st.x_hat, cg_iters)
+    # f1: L1 = Psi^H
+    s1 = ops.psi_adj(st.x_hat)
+    r1 = prox.soft_threshold(s1 + st.z1, st.gamma * w)
+    st.z1 = st.z1 + s1 - r1
+    st.x1 = ops.psi(r1 - st.z1)
+    # f2: L2 = I, positivity
+    r2 = prox.project_positive(st.x_hat + st.z2)
+    st.z2 = st.z2 + st.x_hat - r2
+    st.x2 = r2 - st.z2
+    # f_{i+2}: L = Phi_i, ball B_i
+    s = ops.phi(st.x_hat)
+    nus = []
+    for i in range(R):
+        sl = slice(offsets[i], offsets[i + 1])
+        si = s[sl]
+        ri = prox.project_l2_ball(si + st.zb[i], y[sl], eps[i])
+        st.zb[i] = st.zb[i] + si - ri
+        st.xb[i] = _block_adj(ops, ri - st.zb[i], offsets, i, M)
+        nus.append(float(np.linalg.norm(y[sl] - si) / eps[i]))
+    f1 = float(np.sum(w * np.abs(s1)))
+    zeta = abs(f1 - st.f1_prev) / abs(st.f1_prev) if st.f1_prev != 0.0 else np.inf
+    st.f1_prev = f1
+    st.t += 1
+    rec = {"t": st.t, "f1": f1, "zeta": zeta, "nu": max(nus), "nu_min": min(nus), "nu_blocks": nus,
+           "cg_residual": cg_res}
+    st.history.append(rec)
+    return rec
+
+
+def halted_blocks(rec: dict, xi: float = XI, tau: float = TAU) -> bool:
+    """The halting test of §4.4 with every block's nu_i in the band."""
+    return rec["zeta"] < xi and rec["nu"] <= 1.0 + tau and rec["nu_min"] >= 1.0 - tau
+
+
+def solve_blocks(ops: Operators, y: np.ndarray, eps, offsets, image_shape, coeff_shape, iters: int,
+                 cg_iters: int, beta: float = BETA, weights: np.ndarray | None = None) -> BlockState:
+    """``iters`` SDMM iterations of eq. dbp2 (one reweighting round, fixed count)."""
+    st = init_state_blocks(ops, y, offsets, image_shape, beta)
+    w = np.ones(coeff_shape) if weights is None else np.asarray(weights, dtype=np.float64)
+    for _ in range(iters):
+        sdmm_iteration_blocks(ops, st, y, eps, offsets, w, cg_iters)
+    return st

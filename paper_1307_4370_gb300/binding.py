@@ -55,7 +55,8 @@ class SdmmParams(ctypes.Structure):
 
 class Report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("f1", ctypes.c_double), ("zeta", ctypes.c_double),
-                ("nu", ctypes.c_double), ("gamma", ctypes.c_double), ("cg_residual", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("gamma", ctypes.c_double), ("cg_residual", ctypes.c_double),
+                ("nu_min", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +71,7 @@ _SIGS = {
     "purify_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "purify_last_error": (ctypes.c_char_p, []),
     "purify_set_beam": (_i32, [_vp, _vp, _vp]),
+    "purify_sdmm_set_blocks": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -388,6 +390,22 @@ class SdmmState:
         p.use_graph = int(bool(use_graph))
         _check("purify_sdmm_init", self.lib.purify_sdmm_init(self.c.ctx, self.st, _ptr(y), float(eps),
                                                              ctypes.byref(p), _stream(stream)))
+
+    def set_blocks(self, offsets=None, eps=None, stream=None) -> None:
+        """Distributed-block form: blocks y[offsets[i]:offsets[i+1]] (caller order),
+        one l2 ball of radius eps[i] each; None returns to the single ball."""
+        if offsets is None:
+            _check("purify_sdmm_set_blocks",
+                   self.lib.purify_sdmm_set_blocks(self.c.ctx, self.st, 0, None, None, _stream(stream)))
+            return
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        R = len(e)
+        if off.shape != (R + 1,):
+            raise ValueError("offsets must have len(eps) + 1 entries")
+        _check("purify_sdmm_set_blocks",
+               self.lib.purify_sdmm_set_blocks(self.c.ctx, self.st, R, off.ctypes.data, e.ctypes.data,
+                                               _stream(stream)))
 
     def set_data(self, y, stream=None) -> None:
         _check("purify_sdmm_set_data", self.lib.purify_sdmm_set_data(self.c.ctx, self.st, _ptr(y),

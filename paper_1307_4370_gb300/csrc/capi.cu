@@ -224,6 +224,23 @@ __global__ void k_list_setup(const int2* __restrict__ lk, const float2* __restri
   }
 }
 
+// Distributed form: the block of each sorted visibility (offsets in caller
+// order, R + 1 entries) and the sorted position of each caller index.
+__global__ void k_block_of(const int* __restrict__ perm, int64_t M, const int64_t* __restrict__ offsets, int R,
+                           int* __restrict__ block_of, int* __restrict__ pos) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = perm[j];
+    int lo = 0, hi = R;  // last b with offsets[b] <= m
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= m) lo = mid;
+      else hi = mid - 1;
+    }
+    block_of[j] = lo;
+    pos[m] = (int)j;
+  }
+}
+
 __global__ void k_fill_f32(int64_t n, float* p, float v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -471,6 +488,8 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   da.yb = st->yb;
   da.yscale = st->yscale;
   TRY(degrid(c, kDegridSdmm, da, s));
+  // distributed form (§4.5 eq. dbp1): one ball per block of visibilities
+  if (st->nblocks > 0) TRY(launch_block_norms(st, s));
   // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
   SaraProxArgs pa{st->z1, st->u1, st->w};
   TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
@@ -764,7 +783,8 @@ void purify_sdmm_state_destroy(purify_sdmm_state* st) {
   drop_graph(st);
   if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
   void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->sv, st->x1, st->z3, st->z1, st->u1,
-                  st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v};
+                  st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v,
+                  st->d_block_of, st->d_pos, st->d_bchunks, st->d_beps, st->d_bscale};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete st;
@@ -856,6 +876,62 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   return PURIFY_OK;
 }
 
+int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, const int64_t* offsets,
+                           const double* eps, purify_stream_t stream) {
+  if (!c || !st || st->ctx != c || R < 0 || R > kMaxBlocks) return PURIFY_E_INVALID_ARG;
+  const int64_t M = c->M;
+  if (R > 0) {
+    if (!offsets || !eps || offsets[0] != 0 || offsets[R] != M) return PURIFY_E_INVALID_ARG;
+    for (int b = 0; b < R; ++b)
+      if (offsets[b + 1] <= offsets[b] || !(eps[b] > 0.0)) return PURIFY_E_INVALID_ARG;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY_CUDA(cudaStreamSynchronize(s));
+  drop_graph(st);  // the iteration changes shape: re-capture on the next step
+  void* old[] = {st->d_block_of, st->d_pos, st->d_bchunks, st->d_beps, st->d_bscale};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  st->d_block_of = st->d_pos = nullptr;
+  st->d_bchunks = nullptr;
+  st->d_beps = nullptr;
+  st->d_bscale = nullptr;
+  st->nblocks = 0;
+  st->nbchunks = 0;
+  if (R == 0) return PURIFY_OK;
+  // chunks of at most ch visibilities per block, at most kMaxPartials in all
+  const int64_t ch = std::max<int64_t>(1024, (M + (kMaxPartials - R) - 1) / (kMaxPartials - R));
+  std::vector<int4> chunks;
+  for (int b = 0; b < R; ++b) {
+    const int64_t nb = offsets[b + 1] - offsets[b];
+    const int64_t nc = (nb + ch - 1) / ch;
+    for (int64_t k = 0; k < nc; ++k)
+      chunks.push_back(make_int4(b, (int)(offsets[b] + nb * k / nc), (int)(offsets[b] + nb * (k + 1) / nc), 0));
+  }
+  int64_t* d_off = nullptr;
+  int e;
+  if ((e = dev_alloc(&st->d_block_of, M)) || (e = dev_alloc(&st->d_pos, M)) ||
+      (e = dev_alloc(&st->d_bchunks, (int64_t)chunks.size())) || (e = dev_alloc(&st->d_beps, (int64_t)R)) ||
+      (e = dev_alloc(&st->d_bscale, (int64_t)R)) || (e = dev_alloc(&d_off, (int64_t)R + 1)))
+    return e;
+  int rc = PURIFY_OK;
+  if (cudaMemcpyAsync(d_off, offsets, (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(st->d_beps, eps, R * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(st->d_bchunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    rc = PURIFY_E_CUDA;
+  if (rc == PURIFY_OK) {
+    k_block_of<<<nblk(M), 256, 0, s>>>(c->d_perm, M, d_off, R, st->d_block_of, st->d_pos);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PURIFY_E_CUDA;
+  }
+  cudaFree(d_off);
+  if (rc != PURIFY_OK) return rc;
+  st->nblocks = R;
+  st->nbchunks = (int)chunks.size();
+  return PURIFY_OK;
+}
+
 int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t stream) {
   if (!c || !st || st->ctx != c) return PURIFY_E_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -931,6 +1007,7 @@ int purify_sdmm_get_report(purify_ctx* c, purify_sdmm_state* st, purify_report* 
   rep->f1 = c->h_sc->f1;
   rep->zeta = c->h_sc->zeta;
   rep->nu = c->h_sc->nu;
+  rep->nu_min = c->h_sc->nu_min;
   rep->gamma = c->h_sc->gamma;
   rep->cg_residual = c->h_sc->cg_res;
   return PURIFY_OK;
@@ -950,7 +1027,7 @@ int purify_sdmm_solve(purify_ctx* c, const float* y, double eps, const purify_sd
       rc = purify_sdmm_step(c, st, stream);
       if (rc == PURIFY_OK && st->params.check_every > 0 && (it + 1) % st->params.check_every == 0) {
         rc = purify_sdmm_get_report(c, st, &rep, stream);
-        if (rc == PURIFY_OK && rep.zeta < st->params.xi && rep.nu >= 1.0 - st->params.tau &&
+        if (rc == PURIFY_OK && rep.zeta < st->params.xi && rep.nu_min >= 1.0 - st->params.tau &&
             rep.nu <= 1.0 + st->params.tau)
           break;
       }

@@ -150,6 +150,7 @@ enum CounterSlot {
   kCntMax,         // max |.|
   kCntNorm,        // generic ||a - b||^2
   kCntRho0,        // ||r0||^2 after an SDMM step
+  kCntBlk,         // per-block ||s2 + z2 - y||^2, ||s2 - y||^2 (distributed form)
   kNumCounters
 };
 
@@ -167,7 +168,8 @@ struct DevScalars {
   double norm2;      // generic squared norm
   double gamma;      // penalty
   double eps;        // l2 bound
-  double zeta, nu;   // halting quantities
+  double zeta, nu;   // halting quantities (nu: the largest block's in the distributed form)
+  double nu_min;     // smallest block's nu (= nu for one ball)
   double iters;
   double cg_res;
   int cg_first;      // the next Q-epilogue starts a CG solve
@@ -176,6 +178,7 @@ struct DevScalars {
 };
 
 constexpr int kMaxPartials = 32768;  // blocks per reduction (NV <= 2 values each)
+constexpr int kMaxBlocks = 4096;     // data blocks of the distributed form
 
 // ---------------------------------------------------------------------------
 // Kernel timing: when enabled on a context, every launch is bracketed by two
@@ -337,6 +340,15 @@ struct purify_sdmm_state {
   // CUDA graph of one SDMM step (captured on a private stream, replayed on the caller's)
   cudaStream_t cap_stream;
   cudaGraphExec_t step_exec;
+  // distributed form (§4.5 eq. dbp1): R balls over consecutive caller-order
+  // blocks of the visibilities; nblocks = 0 is the single ball of eq. delta
+  int nblocks;
+  int* d_block_of;          // M, sorted order: block of each visibility
+  int* d_pos;               // M, caller order: sorted position
+  int4* d_bchunks;          // (block, caller begin, caller end, first chunk of the block)
+  int nbchunks;
+  double* d_beps;           // R bounds eps_i
+  float* d_bscale;          // R projection factors min(1, eps_i / ||a_i - y_i||)
   int graph_cg_iters;       // key of the captured graph (cg_iters, data format)
   int graph_beam;           // beam version of the context when it was captured
   int launches_per_step;    // kernels in one captured step
@@ -410,6 +422,7 @@ int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, 
 int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, cudaStream_t s);
 int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s);
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s);
+int launch_block_norms(purify_sdmm_state* st, cudaStream_t s);
 int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round,
                     cudaStream_t s);
 int launch_quantize_bf16(int64_t M, const float2* y, uint16_t* yb, float* yscale, cudaStream_t s);

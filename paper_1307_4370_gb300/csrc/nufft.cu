@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
       sc->l2_dn2 = tot[0];
       sc->l2_res2 = tot[1];
       sc->nu = sqrt(tot[1]) / sc->eps;
+      sc->nu_min = sc->nu;
       const double nd = sqrt(tot[0]);
       sc->l2_scale = (nd > sc->eps) ? sc->eps / nd : 1.0;  // projection factor of the l2 ball
     }

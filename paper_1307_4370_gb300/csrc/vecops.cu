@@ -119,11 +119,15 @@ __global__ void k_max_abs(int64_t n, const float2* __restrict__ a, double* parti
 // left s2 = Phi x_hat and ||s2 + z2 - y||^2 on the device:
 //   a = s2 + z2; r2 = y + min(1, eps/||a - y||)(a - y); z2 <- a - r2;
 //   u2 = r2 - z2; v = u2 - s2 (gridded next: Phi^H v = x2 - Phi^H Phi x_hat).
+// In the distributed form (§4.5 eq. dbp1) each visibility takes the factor
+// of its block (block_of non-null).
 __global__ void k_sdmm_l2(int64_t M, const float2* __restrict__ s2, float2* __restrict__ z2,
                           const float2* __restrict__ y, const uint16_t* __restrict__ yb,
-                          const float* __restrict__ yscale, float2* __restrict__ v, const DevScalars* sc) {
-  const float scale = (float)sc->l2_scale;
+                          const float* __restrict__ yscale, float2* __restrict__ v, const DevScalars* sc,
+                          const int* __restrict__ block_of, const float* __restrict__ bscale) {
+  const float scale1 = (float)sc->l2_scale;
   GRID_STRIDE(i, M) {
+    const float scale = block_of ? bscale[block_of[i]] : scale1;
     float2 yy;
     if (y) {
       yy = y[i];
@@ -138,6 +142,85 @@ __global__ void k_sdmm_l2(int64_t M, const float2* __restrict__ s2, float2* __re
     const float2 zn = csub(a, r2);
     z2[i] = zn;
     v[i] = csub(csub(r2, zn), s);
+  }
+}
+
+// Distributed form (§4.5 eqs. blocks, dbp1): per block i of consecutive
+// caller-order visibilities, ||s2_i + z2_i - y_i||^2 and ||s2_i - y_i||^2
+// (gathered through the sorted positions; exact FP32 terms, FP64 sums).  One
+// CTA per chunk of a block; the last CTA to finish adds each block's chunk
+// partials in chunk order and forms its ball factor min(1, eps_i / ||.||) and
+// nu_i = ||y_i - Phi_i x_hat|| / eps_i (nu = the largest, nu_min the smallest).
+__global__ void __launch_bounds__(256) k_block_norms(const int4* __restrict__ bchunks, int nbchunks,
+                                                     const int* __restrict__ pos, const float2* __restrict__ s2,
+                                                     const float2* __restrict__ z2, const float2* __restrict__ y,
+                                                     const uint16_t* __restrict__ yb,
+                                                     const float* __restrict__ yscale, int R,
+                                                     const double* __restrict__ beps, float* __restrict__ bscale,
+                                                     double* partials, DevScalars* sc) {
+  __shared__ bool am_last;
+  const int4 ch = bchunks[blockIdx.x];
+  FPair part[2];
+  for (int m = ch.y + threadIdx.x; m < ch.z; m += blockDim.x) {
+    const int j = pos[m];
+    float2 yy;
+    if (y) {
+      yy = y[j];
+    } else {
+      const float s4 = yscale[j >> 12];
+      const uint32_t bits = reinterpret_cast<const uint32_t*>(yb)[j];
+      yy = make_float2(__uint_as_float(bits << 16) * s4, __uint_as_float(bits & 0xffff0000u) * s4);
+    }
+    const float2 s = s2[j];
+    const float2 a = cadd(s, z2[j]);
+    part[0].add_sq_diff(a.x, yy.x);
+    part[0].add_sq_diff(a.y, yy.y);
+    part[1].add_sq_diff(s.x, yy.x);
+    part[1].add_sq_diff(s.y, yy.y);
+  }
+  double v[2] = {part[0].value(), part[1].value()};
+  block_reduce<2>(v);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v[0];
+    partials[kMaxPartials + blockIdx.x] = v[1];
+    __threadfence();
+    am_last = atomicAdd(&sc->counter[kCntBlk], 1u) == (unsigned)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double numax = 0.0, numin = INFINITY;
+  for (int b = threadIdx.x; b < R; b += blockDim.x) {
+    // chunks of block b: from its first chunk up to the next block's first
+    int k0 = 0;
+    {
+      int lo = 0, hi = nbchunks;  // first chunk whose block is >= b
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (bchunks[mid].x < b) lo = mid + 1;
+        else hi = mid;
+      }
+      k0 = lo;
+    }
+    double dn2 = 0.0, res2 = 0.0;
+    for (int k = k0; k < nbchunks && bchunks[k].x == b; ++k) {
+      dn2 += __ldcg(&partials[k]);
+      res2 += __ldcg(&partials[kMaxPartials + k]);
+    }
+    const double e = beps[b];
+    const double nd = sqrt(dn2);
+    bscale[b] = (float)(nd > e ? e / nd : 1.0);
+    const double nu = sqrt(res2) / e;
+    numax = fmax(numax, nu);
+    numin = fmin(numin, nu);
+  }
+  double mx[1] = {numax}, mn[1] = {-numin};
+  block_reduce<1, true>(mx);
+  block_reduce<1, true>(mn);
+  if (threadIdx.x == 0) {
+    sc->nu = mx[0];
+    sc->nu_min = -mn[0];
+    sc->counter[kCntBlk] = 0u;
   }
 }
 
@@ -229,8 +312,20 @@ int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s
 
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s) {
   purify_ctx* c = st->ctx;
+  const bool blk = st->nblocks > 0;
   PURIFY_LAUNCH(st->ctx, "sdmm_l2", s, (k_sdmm_l2<<<blocks_for(c->M), 256, 0, s>>>(c->M, st->s2, st->z2, st->y_bf16 ? nullptr : st->y, st->yb,
-                                             st->yscale, st->v, c->d_sc)));
+                                             st->yscale, st->v, c->d_sc, blk ? st->d_block_of : nullptr,
+                                             blk ? st->d_bscale : nullptr)));
+  return check_cuda(cudaGetLastError());
+}
+
+int launch_block_norms(purify_sdmm_state* st, cudaStream_t s) {
+  purify_ctx* c = st->ctx;
+  PURIFY_LAUNCH(c, "block_norms", s,
+                (k_block_norms<<<st->nbchunks, 256, 0, s>>>(st->d_bchunks, st->nbchunks, st->d_pos, st->s2, st->z2,
+                                                            st->y_bf16 ? nullptr : st->y, st->yb, st->yscale,
+                                                            st->nblocks, st->d_beps, st->d_bscale,
+                                                            c->d_partials + kCntBlk * 2 * kMaxPartials, c->d_sc)));
   return check_cuda(cudaGetLastError());
 }
 

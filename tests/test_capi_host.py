@@ -82,5 +82,6 @@ def test_null_arguments(lib):
     assert lib.purify_phi(None, None, None, None) == -1
     assert lib.purify_sdmm_step(None, None, None) == -1
     assert lib.purify_set_beam(None, None, None) == -1
+    assert lib.purify_sdmm_set_blocks(None, None, 0, None, None, None) == -1
     lib.purify_destroy(None)
     lib.purify_sdmm_state_destroy(None)

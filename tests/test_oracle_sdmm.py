@@ -144,3 +144,82 @@ def test_noise_model():
     eps = simulate.l2_bound(M, sig)
     assert np.mean(norms <= eps) > 0.9
     assert eps ** 2 == pytest.approx(M * sig ** 2 + 2 * np.sqrt(M) * sig ** 2, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Distributed-block form (§4.5 eqs. blocks, dbp1, dbp2)
+# ---------------------------------------------------------------------------
+def slsqp_blocks_reference(A, y, eps, offsets, Wm):
+    """min ||Wm x||_1 s.t. ||y_i - A_i x|| <= eps_i for every block, x >= 0."""
+    D = Wm.shape[0]
+    WT = Wm.T
+    cons = [{"type": "ineq", "fun": lambda v: WT @ (v[:D] - v[D:])}]
+    for i in range(len(eps)):
+        Ai = A[offsets[i]:offsets[i + 1]]
+        Ar = np.vstack([Ai.real, Ai.imag])
+        yr = np.concatenate([y[offsets[i]:offsets[i + 1]].real, y[offsets[i]:offsets[i + 1]].imag])
+
+        def l2(v, Ar=Ar, yr=yr, e=eps[i]):
+            r = yr - Ar @ (WT @ (v[:D] - v[D:]))
+            return e ** 2 - r @ r
+        cons.append({"type": "ineq", "fun": l2})
+    res = optimize.minimize(lambda v: v.sum(), np.full(2 * D, 0.1), method="SLSQP",
+                            bounds=[(0, None)] * (2 * D), constraints=cons,
+                            options={"maxiter": 3000, "ftol": 1e-14})
+    for c in cons[1:]:
+        assert c["fun"](res.x) >= -1e-9 * max(eps) ** 2
+    return res.fun
+
+
+@pytest.mark.parametrize("offsets_frac", [(0, 0.5, 1.0), (0, 0.3, 0.55, 1.0)])
+def test_block_sdmm_reaches_constrained_minimum(offsets_frac):
+    A, y, eps, n = tiny_problem(seed=12)
+    M = len(y)
+    offsets = [int(round(f * M)) for f in offsets_frac]
+    # per-block bounds: the single ball's budget split in proportion to M_i, tightened
+    # so that the block constraints bind differently from the single ball
+    eps_b = [eps * np.sqrt((offsets[i + 1] - offsets[i]) / M) * (0.9 if i == 0 else 1.05)
+             for i in range(len(offsets) - 1)]
+    Wm = np.eye(n * n)
+    ops = dense_ops(A, Wm, n, 1)
+    st = sdmm.init_state_blocks(ops, y, offsets, (n, n))
+    w = np.ones((1, n, n))
+    for _ in range(3000):
+        rec = sdmm.sdmm_iteration_blocks(ops, st, y, eps_b, offsets, w, 10)
+    x = st.x_hat
+    assert np.max(np.abs(x.imag)) < 1e-8 and x.real.min() > -1e-8
+    f_ref = slsqp_blocks_reference(A, y, eps_b, offsets, Wm)
+    assert np.abs(x.real).sum() == pytest.approx(f_ref, rel=1e-6)
+    for i, e in enumerate(eps_b):
+        sl = slice(offsets[i], offsets[i + 1])
+        assert np.linalg.norm(y[sl] - A[sl] @ x.real.ravel()) <= e * (1 + 1e-6)
+    assert rec["nu"] == max(rec["nu_blocks"]) and rec["nu_min"] == min(rec["nu_blocks"])
+
+
+def test_one_block_is_the_single_ball():
+    p = inputs.make_problem(inputs.Workload("b32", n=32, M=800, J=4, n_src=5, diffuse=False, seed=4))
+    w = p.workload
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, 30.0)
+    ops = simulate.operators(p.uv, w.n, w.J)
+    a = sdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=8, cg_iters=10)
+    b = sdmm.solve_blocks(ops, y, [eps], [0, w.M], (w.n, w.n), (9, w.n, w.n), iters=8, cg_iters=10)
+    assert np.linalg.norm(a.x_hat - b.x_hat) <= 1e-12 * np.linalg.norm(a.x_hat)
+    for ha, hb in zip(a.history, b.history):
+        assert hb["nu"] == pytest.approx(ha["nu"], rel=1e-12)
+        assert hb["f1"] == pytest.approx(ha["f1"], rel=1e-12)
+
+
+def test_block_projection():
+    rng = np.random.default_rng(3)
+    M = 60
+    offsets = [0, 20, 45, 60]
+    y = inputs.random_vis(M, rng)
+    r = y + 2.0 * inputs.random_vis(M, rng)
+    eps = [0.5, 100.0, 1.0]
+    out = sdmm.prox.project_l2_balls(r, y, eps, offsets)
+    for i, e in enumerate(eps):
+        sl = slice(offsets[i], offsets[i + 1])
+        assert np.linalg.norm(out[sl] - y[sl]) <= e * (1 + 1e-14)
+        assert np.allclose(out[sl], sdmm.prox.project_l2_ball(r[sl], y[sl], e), rtol=0, atol=0)
+    assert np.array_equal(out[20:45], r[20:45])   # block 2 was inside its ball
+    assert np.allclose(sdmm.prox.project_l2_balls(out, y, eps, offsets), out, rtol=0, atol=1e-15)
