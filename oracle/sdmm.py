@@ -49,6 +49,7 @@ import numpy as np
 
 from . import cg as cg_mod
 from . import prox
+from . import tv as tv_mod
 
 BETA = 1e-3
 XI = 1e-3
@@ -269,4 +270,81 @@ def solve_blocks(ops: Operators, y: np.ndarray, eps, offsets, image_shape, coeff
     w = np.ones(coeff_shape) if weights is None else np.asarray(weights, dtype=np.float64)
     for _ in range(iters):
         sdmm_iteration_blocks(ops, st, y, eps, offsets, w, cg_iters)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# TV prior (§3.3 eq. tvproblem with the positivity of §6's "TV", §5 weighted TV)
+# ---------------------------------------------------------------------------
+# Algorithm 1 with S = 3: L1 = I and f1 = ||W grad .||_1 (prox by FGP,
+# ``tv.prox_tv``), L2 = Phi with the l2 ball, L3 = I with positivity.  Q is
+# again Phi^H Phi + 2I.  Readings: gamma = beta max_j |grad(Phi^H y)|_j (the
+# l1 rule of §4.4 with the TV operator in place of Psi^H); the TV weights of
+# reweighting round r are delta_r / (delta_r + |grad x_hat|) with delta_r as
+# for SARA.
+
+
+def penalty_tv(ops: Operators, y: np.ndarray, beta: float = BETA) -> float:
+    """gamma = beta max |grad(Phi^H y)|."""
+    return float(beta * np.max(tv_mod.grad_magnitude(ops.phi_adj(y))))
+
+
+def init_state_tv(ops: Operators, y: np.ndarray, image_shape, beta: float = BETA) -> State:
+    """Algorithm 1 steps 1-3 for the TV problem with x_hat(0) = 0."""
+    x0 = np.zeros(image_shape, dtype=np.complex128)
+    return State(x_hat=x0, z1=x0.copy(), z2=np.zeros_like(ops.phi(x0)), z3=x0.copy(), x1=x0.copy(),
+                 x2=ops.phi_adj(np.zeros_like(ops.phi(x0))), x3=x0.copy(), gamma=penalty_tv(ops, y, beta))
+
+
+def sdmm_iteration_tv(ops: Operators, st: State, y: np.ndarray, eps: float, w: np.ndarray | None,
+                      cg_iters: int, fgp_iters: int = tv_mod.FGP_ITERS) -> dict:
+    """One pass of Algorithm 1 steps 5-9 for the (weighted) TV problem."""
+    def apply_q(v):
+        return ops.phi_adj(ops.phi(v)) + 2.0 * v
+
+    b = st.x1 + st.x2 + st.x3
+    st.x_hat, cg_res = cg_mod.cg(apply_q, b, st.x_hat, cg_iters)
+    # i = 1 (L1 = I, f1 = ||W grad .||_1)
+    r1 = tv_mod.prox_tv(st.x_hat + st.z1, st.gamma, w, fgp_iters)
+    st.z1 = st.z1 + st.x_hat - r1
+    st.x1 = r1 - st.z1
+    # i = 2 (l2 ball), i = 3 (positivity): as for SARA
+    s2 = ops.phi(st.x_hat)
+    r2 = prox.project_l2_ball(s2 + st.z2, y, eps)
+    st.z2 = st.z2 + s2 - r2
+    st.x2 = ops.phi_adj(r2 - st.z2)
+    r3 = prox.project_positive(st.x_hat + st.z3)
+    st.z3 = st.z3 + st.x_hat - r3
+    st.x3 = r3 - st.z3
+    f1 = tv_mod.tv_norm(st.x_hat, w)
+    zeta = abs(f1 - st.f1_prev) / abs(st.f1_prev) if st.f1_prev != 0.0 else np.inf
+    nu = float(np.linalg.norm(y - s2) / eps)
+    st.f1_prev = f1
+    st.t += 1
+    rec = {"t": st.t, "f1": f1, "zeta": zeta, "nu": nu, "cg_residual": cg_res}
+    st.history.append(rec)
+    return rec
+
+
+def reweight_tv(x_hat: np.ndarray, round_index: int) -> np.ndarray:
+    """TV weights of reweighting round ``round_index`` >= 1."""
+    g = tv_mod.grad_magnitude(x_hat)
+    gmax = float(g.max())
+    delta = max(10.0 ** (-round_index) * gmax, 1e-6 * gmax)
+    if delta == 0.0:
+        return np.ones_like(g)
+    return delta / (delta + g)
+
+
+def solve_tv(ops: Operators, y: np.ndarray, eps: float, image_shape, iters: int, cg_iters: int,
+             rounds: int = 1, fgp_iters: int = tv_mod.FGP_ITERS, beta: float = BETA) -> State:
+    """``rounds`` reweighting rounds (TV, then RWTV) of ``iters`` SDMM iterations each."""
+    st = init_state_tv(ops, y, image_shape, beta)
+    w = np.ones(image_shape)
+    for rnd in range(rounds):
+        if rnd > 0:
+            w = reweight_tv(st.x_hat, rnd)
+        for _ in range(iters):
+            sdmm_iteration_tv(ops, st, y, eps, w, cg_iters, fgp_iters)
+    st.weights = w
     return st

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 from scipy import optimize
 
-from oracle import measurement as me, sara, sdmm, simulate
+from oracle import measurement as me, sara, sdmm, simulate, tv
 from paper_1307_4370_gb300 import inputs
 
 
@@ -223,3 +223,49 @@ def test_block_projection():
         assert np.allclose(out[sl], sdmm.prox.project_l2_ball(r[sl], y[sl], e), rtol=0, atol=0)
     assert np.array_equal(out[20:45], r[20:45])   # block 2 was inside its ball
     assert np.allclose(sdmm.prox.project_l2_balls(out, y, eps, offsets), out, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# TV prior (§3.3 eq. tvproblem with positivity; prox by FGP)
+# ---------------------------------------------------------------------------
+def smoothed_tv_reference(A, y, eps, n, x0):
+    """Independent solver: min sum sqrt(|grad x|^2 + mu^2) s.t. ||y - A x|| <= eps,
+    x >= 0 (SLSQP on the smooth problem, mu continued down to 1e-5)."""
+    Ar = np.vstack([A.real, A.imag])
+    yr = np.concatenate([y.real, y.imag])
+    v = np.maximum(x0, 0.0)
+    for mu in (1e-2, 1e-3, 1e-4, 1e-5):
+        def f(v, mu=mu):
+            d1, d2 = tv.grad(v.reshape(n, n))
+            return np.sum(np.sqrt(d1 ** 2 + d2 ** 2 + mu ** 2))
+        v = optimize.minimize(f, v, method="SLSQP", bounds=[(0, None)] * (n * n),
+                              constraints=[{"type": "ineq", "fun": lambda v: eps ** 2 - np.sum((yr - Ar @ v) ** 2)}],
+                              options={"maxiter": 5000, "ftol": 1e-15}).x
+    assert np.sum((yr - Ar @ v) ** 2) <= eps ** 2 * (1 + 1e-9) and v.min() >= -1e-12
+    return v
+
+
+def test_tv_sdmm_reaches_constrained_minimum():
+    A, y, eps, n = tiny_problem(seed=13)
+    ops = dense_ops(A, np.eye(n * n), n, 1)
+    st = sdmm.init_state_tv(ops, y, (n, n))
+    for _ in range(3000):
+        sdmm.sdmm_iteration_tv(ops, st, y, eps, None, 10, 50)
+    x = st.x_hat
+    assert np.max(np.abs(x.imag)) < 1e-6 and x.real.min() > -1e-6
+    assert np.linalg.norm(y - A @ x.real.ravel()) <= eps * (1 + 1e-6)
+    v = smoothed_tv_reference(A, y, eps, n, x.real.ravel())
+    tv_sdmm, tv_ref = tv.tv_norm(x.real), tv.tv_norm(v.reshape(n, n))
+    assert tv_sdmm == pytest.approx(tv_ref, rel=2e-5)
+    assert tv_sdmm <= tv_ref * (1 + 1e-6)
+    assert st.gamma == pytest.approx(1e-3 * np.max(tv.grad_magnitude((A.conj().T @ y).reshape(n, n))))
+
+
+def test_tv_reweighting_rule():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((8, 8))
+    w = sdmm.reweight_tv(x, 2)
+    g = tv.grad_magnitude(x)
+    delta = 1e-2 * g.max()
+    assert np.allclose(w, delta / (delta + g), rtol=1e-15, atol=0)
+    assert np.all(sdmm.reweight_tv(np.ones((4, 4)), 1) == 1.0)
