@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--kernel", choices=["kb", "gauss"], default="kb",
                     help="interpolation kernel of G: Kaiser-Bessel or the paper's Gaussian")
+    ap.add_argument("--prior", choices=["sara", "tv"], default="sara",
+                    help="SARA (eq. delta) or the TV prior with positivity (FGP prox, 20 inner iterations)")
     ap.add_argument("--blocks", type=int, default=0,
                     help="distributed-block form (one l2 ball per block of equal size); 0 = one ball")
     ap.add_argument("--precision", choices=["c64", "bf16"], default="c64",
@@ -80,7 +82,7 @@ def block_table(M: int, R: int, eps: float):
 
 
 def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = None, kernel: str = "kb",
-                blocks: int = 0):
+                blocks: int = 0, prior: str = "sara"):
     """SDMM iterations/s of the FP64 oracle on a bounded sample of the workload."""
     from oracle import sdmm as osdmm, simulate
 
@@ -88,7 +90,13 @@ def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = Non
     y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db, kernel=kernel)
     ops = simulate.operators(p.uv, w.n, w.J, kernel=kernel)
     wts = np.ones((9, w.n, w.n))
-    if blocks > 0:
+    if prior == "tv":
+        st = osdmm.init_state_tv(ops, y, (w.n, w.n))
+        wtv = np.ones((w.n, w.n))
+
+        def iteration():
+            osdmm.sdmm_iteration_tv(ops, st, y, eps, wtv, w.cg_iters)
+    elif blocks > 0:
         offsets, eps_b = block_table(w.M, blocks, eps)
         st = osdmm.init_state_blocks(ops, y, offsets, (w.n, w.n))
 
@@ -110,8 +118,9 @@ def oracle_rate(w: inputs.Workload, budget_s: float, max_iters: int | None = Non
     return done / el, done, el
 
 
-def cpu_baseline_entry(w, budget_s, max_iters=None, kernel: str = "kb", blocks: int = 0) -> dict:
-    rate, done, el = oracle_rate(w, budget_s, max_iters, kernel, blocks)
+def cpu_baseline_entry(w, budget_s, max_iters=None, kernel: str = "kb", blocks: int = 0,
+                       prior: str = "sara") -> dict:
+    rate, done, el = oracle_rate(w, budget_s, max_iters, kernel, blocks, prior)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} SDMM iterations (after one untimed) of the {w.name} workload, FP64 numpy "
                       f"oracle, single thread, {el:.1f} s; host has {os.cpu_count()} cores"}
@@ -123,12 +132,12 @@ def run_reference(args, w):
         return
     # bounded: about a minute of oracle work whatever --steps is
     budget = min(60.0, max(10.0, 0.2 * (args.steps + args.warmup)))
-    entry = cpu_baseline_entry(w, budget, kernel=args.kernel, blocks=args.blocks)
+    entry = cpu_baseline_entry(w, budget, kernel=args.kernel, blocks=args.blocks, prior=args.prior)
     out = {"impl": "reference", "metric": METRIC, "value": entry["value"], "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 / entry["value"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {**workload_config(w), "kernel": args.kernel, "blocks": args.blocks},
+           "config": {**workload_config(w), "prior": args.prior, "kernel": args.kernel, "blocks": args.blocks},
            "cpu_baseline": entry,
            "e2e": {"value": entry["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -213,11 +222,16 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
         "dwt_level": (N * c + D * (c + 4 + 2 * c)) / 4,
         "idwt_level": (D * c + N * c) / 4,
         "dirac": 4 * N * c,
+        # TV prior: one FGP iteration reads b, r, s, p, q, w and writes p, q, r', s';
+        # the finishing pass reads b, p, q, x_hat, w and writes z1, x1
+        "tv_fgp": 9 * N * c + 4 * N,
+        "tv_finish": 6 * N * c + 4 * N,
+        "tv_init": 7 * N * c,
     }
 
 
 KERNEL_SOURCE = {"row_fwd": "nufft.cu", "col_fwd": "nufft.cu", "degrid": "nufft.cu", "grid": "nufft.cu",
-                 "gram": "nufft.cu",
+                 "gram": "nufft.cu", "tv_fgp": "tv.cu", "tv_finish": "tv.cu", "tv_init": "tv.cu",
                  "col_inv": "nufft.cu", "row_inv": "nufft.cu", "dwt_level": "sara.cu", "idwt_level": "sara.cu",
                  "dirac": "sara.cu", "sdmm_l2": "vecops.cu"}
 
@@ -284,7 +298,8 @@ def run_gpu(args, w):
 
     cpu_entry = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds, kernel=args.kernel, blocks=args.blocks)
+        cpu_entry = cpu_baseline_entry(w, args.cpu_seconds, kernel=args.kernel, blocks=args.blocks,
+                                       prior=args.prior)
 
     # each rank: its own independent problem of the same shape
     p = inputs.make_problem(rank_workload(w, rank))
@@ -298,6 +313,8 @@ def run_gpu(args, w):
     y = y0 + sig * noise
     eps = binding.l2_bound(w.M, sig)
     st = ctx.sdmm_state()
+    if args.prior == "tv":
+        st.set_prior("tv")
     st.init(y, eps, cg_iters=w.cg_iters)
     if args.blocks > 0:
         st.set_blocks(*block_table(w.M, args.blocks, eps))
@@ -408,7 +425,7 @@ def run_gpu(args, w):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {**workload_config(w), "kernel": args.kernel, "blocks": args.blocks,
+            "config": {**workload_config(w), "prior": args.prior, "kernel": args.kernel, "blocks": args.blocks,
                        "y_storage": args.precision,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "cuda_graph": True, "tile": tune["tile"], "tile_ms": tune["timings"],

@@ -85,6 +85,14 @@ typedef enum {
   PURIFY_KERNEL_GAUSS = 1
 } purify_kernel;
 
+/* Prior of the SDMM problem: SARA (eq. delta, the context's dictionary) or
+ * the (weighted) TV of eq. tvproblem with positivity (§3.3, §5, §6 "TV" and
+ * "RWTV"). */
+typedef enum {
+  PURIFY_PRIOR_SARA = 0,
+  PURIFY_PRIOR_TV = 1
+} purify_prior;
+
 typedef enum {
   PURIFY_VIS_C64 = 0,       /* complex64 */
   PURIFY_VIS_BF16_BLOCK = 1 /* bf16 (re, im) pairs, one float32 scale per 4096 */
@@ -278,6 +286,26 @@ int purify_sdmm_set_data_bf16(purify_ctx* ctx, purify_sdmm_state* st, const floa
 
 /* One SDMM iteration (Algorithm 1 steps 5-9). */
 int purify_sdmm_step(purify_ctx* ctx, purify_sdmm_state* st, purify_stream_t stream);
+
+/* Prior of an SDMM state (default PURIFY_PRIOR_SARA).  PURIFY_PRIOR_TV runs
+ * Algorithm 1 with L1 = I and f1 = ||W grad x||_1 (isotropic forward
+ * differences, zero on the last row and column; W the state's N weights, 1
+ * until reweighted by purify_sdmm_reweight with delta / (delta + |grad x_hat|));
+ * its prox is `fgp_iters` (1..1000) iterations of Beck & Teboulle's fast
+ * gradient projection on the dual (§5), and gamma = beta max |grad Phi^H y|.
+ * Call before purify_sdmm_init.  Allocates the prox scratch (7 N complex64)
+ * on the context.  PURIFY_E_INVALID_ARG for an unknown prior or iteration
+ * count. */
+int purify_sdmm_set_prior(purify_ctx* ctx, purify_sdmm_state* st, int32_t prior,
+                          int32_t fgp_iters);
+
+/* prox of lambda ||W grad .||_1 (§5): out = argmin 1/2 ||x - in||^2 +
+ * lambda ||W grad x||_1 by `iters` FGP iterations (0 returns in).  in, out:
+ * N complex64 (device, may not alias); w: N float32 weights > 0 (device) or
+ * NULL for W = I; lambda >= 0.  Uses the context's TV scratch (allocated on
+ * first use). */
+int purify_prox_tv(purify_ctx* ctx, const float* in, const float* w, float lambda,
+                   int32_t iters, float* out, purify_stream_t stream);
 
 /* Distributed-block form (§4.5 eqs. blocks, dbp1, dbp2): the visibilities,
  * in the caller's order, are cut into R consecutive blocks y_1 .. y_R with

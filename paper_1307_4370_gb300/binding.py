@@ -72,6 +72,8 @@ _SIGS = {
     "purify_last_error": (ctypes.c_char_p, []),
     "purify_set_beam": (_i32, [_vp, _vp, _vp]),
     "purify_sdmm_set_blocks": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "purify_sdmm_set_prior": (_i32, [_vp, _vp, _i32, _i32]),
+    "purify_prox_tv": (_i32, [_vp, _vp, _vp, ctypes.c_float, _i32, _vp, _vp]),
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -275,6 +277,17 @@ class Context:
                                                   float(gamma), _ptr(out), _stream(stream)))
         return out
 
+    def prox_tv(self, x: torch.Tensor, w: torch.Tensor | None, lam: float, iters: int = 20,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """prox of lam ||W grad .||_1 by `iters` FGP iterations (x: n x n complex64)."""
+        x = x.contiguous()
+        out = out if out is not None else torch.empty_like(x)
+        if w is not None and (w.dtype != torch.float32 or w.numel() != self.N):
+            raise ValueError("w: float32, one weight per pixel")
+        _check("purify_prox_tv", self.lib.purify_prox_tv(self.ctx, _ptr(x), _ptr(w), float(lam), int(iters),
+                                                         _ptr(out), _stream(stream)))
+        return out
+
     def proj_l2ball(self, r: torch.Tensor, y: torch.Tensor, eps: float, out: torch.Tensor | None = None,
                     norm_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         out = out if out is not None else torch.empty_like(r)
@@ -390,6 +403,11 @@ class SdmmState:
         p.use_graph = int(bool(use_graph))
         _check("purify_sdmm_init", self.lib.purify_sdmm_init(self.c.ctx, self.st, _ptr(y), float(eps),
                                                              ctypes.byref(p), _stream(stream)))
+
+    def set_prior(self, prior: str = "sara", fgp_iters: int = 20) -> None:
+        """"sara" (eq. delta) or "tv" (eq. tvproblem with positivity); before init()."""
+        code = {"sara": 0, "tv": 1}[prior]
+        _check("purify_sdmm_set_prior", self.lib.purify_sdmm_set_prior(self.c.ctx, self.st, code, int(fgp_iters)))
 
     def set_blocks(self, offsets=None, eps=None, stream=None) -> None:
         """Distributed-block form: blocks y[offsets[i]:offsets[i+1]] (caller order),

@@ -263,7 +263,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -490,13 +490,19 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   TRY(degrid(c, kDegridSdmm, da, s));
   // distributed form (§4.5 eq. dbp1): one ball per block of visibilities
   if (st->nblocks > 0) TRY(launch_block_norms(st, s));
-  // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
-  SaraProxArgs pa{st->z1, st->u1, st->w};
-  TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
-  // i = 2, second half: ball projection, z2 update, v = u2 - s2
-  TRY(launch_sdmm_l2_update(st, s));
-  // x1 = Psi u1
-  TRY(sara_synthesis(c, st->u1, st->x1, s));
+  if (st->prior == PURIFY_PRIOR_TV) {
+    // i = 1, TV prior (L1 = I): r1 = prox of gamma ||W grad .||_1 at x_hat + z1, z1, x1 = r1 - z1
+    TRY(tv_sdmm_branch(c, st, s));
+    TRY(launch_sdmm_l2_update(st, s));
+  } else {
+    // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
+    SaraProxArgs pa{st->z1, st->u1, st->w};
+    TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
+    // i = 2, second half: ball projection, z2 update, v = u2 - s2
+    TRY(launch_sdmm_l2_update(st, s));
+    // x1 = Psi u1
+    TRY(sara_synthesis(c, st->u1, st->x1, s));
+  }
   // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual
   TRY(grid_adjoint(c, kGridSorted, st->v, s));
   RowOutArgs ra{};
@@ -865,15 +871,45 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   RowOutArgs ra{};
   ra.out = st->x1;
   TRY(phi_adjoint_image(c, kRowOutPlain, ra, s));
-  SaraProxArgs pa{};
-  TRY(sara_analysis(c, st->x1, st->u1, kSaraPlain, pa, s));
-  TRY(launch_max_abs(c, D, st->u1, s));
+  if (st->prior == PURIFY_PRIOR_TV) {
+    // TV: gamma = beta max |grad Phi^H y|
+    float2* g = nullptr;
+    TRY(tv_gradmag(c, st->x1, &g, s));
+    TRY(launch_max_abs(c, N, g, s));
+  } else {
+    SaraProxArgs pa{};
+    TRY(sara_analysis(c, st->x1, st->u1, kSaraPlain, pa, s));
+    TRY(launch_max_abs(c, D, st->u1, s));
+  }
   TRY(launch_set_gamma(c, st->params.beta, s));
   TRY_CUDA(cudaMemsetAsync(st->x1, 0, N * sizeof(float2), s));
   TRY_CUDA(cudaMemsetAsync(st->u1, 0, D * sizeof(float2), s));
   // the host staging copy of the scalars must land before h_sc is reused
   TRY_CUDA(cudaStreamSynchronize(s));
   return PURIFY_OK;
+}
+
+int purify_sdmm_set_prior(purify_ctx* c, purify_sdmm_state* st, int32_t prior, int32_t fgp_iters) {
+  if (!c || !st || st->ctx != c) return PURIFY_E_INVALID_ARG;
+  if (prior != PURIFY_PRIOR_SARA && prior != PURIFY_PRIOR_TV) return PURIFY_E_INVALID_ARG;
+  if (prior == PURIFY_PRIOR_TV && (fgp_iters < 1 || fgp_iters > 1000)) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (prior == PURIFY_PRIOR_TV) {
+    float2* scr = nullptr;
+    TRY(tv_scratch_ready(c, &scr));
+  }
+  drop_graph(st);
+  st->prior = prior;
+  st->fgp_iters = prior == PURIFY_PRIOR_TV ? fgp_iters : 0;
+  return PURIFY_OK;
+}
+
+int purify_prox_tv(purify_ctx* c, const float* in, const float* w, float lambda, int32_t iters, float* out,
+                   purify_stream_t stream) {
+  if (!c || !in || !out || !(lambda >= 0.0f) || iters < 0 || iters > 100000) return PURIFY_E_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(in) || !is_device_ptr(out) || (w && !is_device_ptr(w))) return PURIFY_E_NOT_DEVICE_PTR;
+  return tv_prox(c, (const float2*)in, w, lambda, iters, (float2*)out, (cudaStream_t)stream);
 }
 
 int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, const int64_t* offsets,
@@ -974,6 +1010,13 @@ int purify_sdmm_reweight(purify_ctx* c, purify_sdmm_state* st, int32_t round, pu
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t D = ctx_D(c);
+  if (st->prior == PURIFY_PRIOR_TV) {
+    // TV weights delta / (delta + |grad x_hat|) (same rule as SARA's)
+    float2* g = nullptr;
+    TRY(tv_gradmag(c, st->xhat, &g, s));
+    TRY(launch_max_abs(c, ctx_N(c), g, s));
+    return launch_reweight(c, ctx_N(c), g, st->w, round, s);
+  }
   SaraProxArgs pa{};
   TRY(sara_analysis(c, st->xhat, st->u1, kSaraPlain, pa, s));
   TRY(launch_max_abs(c, D, st->u1, s));

@@ -226,6 +226,7 @@ struct purify_ctx {
   int device;
   int n, L, J, levels, q;
   int kernel;           // PURIFY_KERNEL_KB or PURIFY_KERNEL_GAUSS
+  float2* d_tv;         // 7 N scratch of the TV prox (input, two dual pairs ping-ponged, last dual pair)
   float* d_beam;        // primary beam B (N floats), allocated by the first purify_set_beam
   bool beam_on;         // B applied (otherwise B = I)
   int beam_version;     // bumped by every purify_set_beam (graphs re-capture)
@@ -349,6 +350,8 @@ struct purify_sdmm_state {
   int nbchunks;
   double* d_beps;           // R bounds eps_i
   float* d_bscale;          // R projection factors min(1, eps_i / ||a_i - y_i||)
+  int prior;                // PURIFY_PRIOR_SARA or PURIFY_PRIOR_TV
+  int fgp_iters;            // TV prox inner iterations
   int graph_cg_iters;       // key of the captured graph (cg_iters, data format)
   int graph_beam;           // beam version of the context when it was captured
   int launches_per_step;    // kernels in one captured step
@@ -423,6 +426,10 @@ int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, fl
 int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s);
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s);
 int launch_block_norms(purify_sdmm_state* st, cudaStream_t s);
+int tv_sdmm_branch(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s);
+int tv_scratch_ready(purify_ctx* c, float2** out);
+int tv_gradmag(purify_ctx* c, const float2* x, float2** g, cudaStream_t s);
+int tv_prox(purify_ctx* c, const float2* in, const float* w, float lam, int iters, float2* out, cudaStream_t s);
 int launch_reweight(purify_ctx* c, int64_t count, const float2* alpha, float* w, int round,
                     cudaStream_t s);
 int launch_quantize_bf16(int64_t M, const float2* y, uint16_t* yb, float* yscale, cudaStream_t s);

@@ -83,5 +83,7 @@ def test_null_arguments(lib):
     assert lib.purify_sdmm_step(None, None, None) == -1
     assert lib.purify_set_beam(None, None, None) == -1
     assert lib.purify_sdmm_set_blocks(None, None, 0, None, None, None) == -1
+    assert lib.purify_sdmm_set_prior(None, None, 1, 20) == -1
+    assert lib.purify_prox_tv(None, None, None, ctypes.c_float(1.0), 20, None, None) == -1
     lib.purify_destroy(None)
     lib.purify_sdmm_state_destroy(None)
