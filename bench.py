@@ -230,8 +230,8 @@ def algorithmic_bytes(w: inputs.Workload, q: int = 9) -> dict:
     }
 
 
-KERNEL_SOURCE = {"row_fwd": "nufft.cu", "col_fwd": "nufft.cu", "degrid": "nufft.cu", "grid": "nufft.cu",
-                 "gram": "nufft.cu", "tv_fgp": "tv.cu", "tv_finish": "tv.cu", "tv_init": "tv.cu",
+KERNEL_SOURCE = {"row_fwd": "nufft.cu", "col_fwd": "nufft.cu", "degrid": "gridding.cu", "grid": "gridding.cu",
+                 "gram": "gridding.cu", "tv_fgp": "tv.cu", "tv_finish": "tv.cu", "tv_init": "tv.cu",
                  "col_inv": "nufft.cu", "row_inv": "nufft.cu", "dwt_level": "sara.cu", "idwt_level": "sara.cu",
                  "dirac": "sara.cu", "sdmm_l2": "vecops.cu"}
 
@@ -246,7 +246,10 @@ def dram_traffic(workload: str, kernel: str):
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if src is None or not os.path.exists(path):
         return None
-    with open(os.path.join(ROOT, "paper_1307_4370_gb300", "csrc", src), "rb") as f:
+    src_path = os.path.join(ROOT, "paper_1307_4370_gb300", "csrc", src)
+    if not os.path.exists(src_path):
+        return None
+    with open(src_path, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
     with open(path) as f:
         for ln in f:

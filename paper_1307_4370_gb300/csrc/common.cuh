@@ -177,6 +177,13 @@ struct DevScalars {
   unsigned int counter[kNumCounters];
 };
 
+// Static plus dynamic shared memory above 48 KB needs a per-kernel opt-in
+// (the kernels' static shared memory is well under 8 KB).
+template <class K>
+inline void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 constexpr int kMaxPartials = 32768;  // blocks per reduction (NV <= 2 values each)
 constexpr int kMaxBlocks = 4096;     // data blocks of the distributed form
 

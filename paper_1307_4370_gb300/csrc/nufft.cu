@@ -1,15 +1,13 @@
-// Measurement operator Phi = G F D Z (§5 eq. opmodel, B = I) and its adjoint.
+// The FFT side of Phi = G F D Z B (§5 eq. opmodel) and its adjoint; the
+// interpolation G and G^T are in gridding.cu.
 //
-// Forward:  k_row_fwd   D Z and the row DFTs of the n non-zero grid rows
+// Forward:  k_row_fwd   B, D, Z and the row DFTs of the n non-zero grid rows
 //                       (the zero padding is never written);
-//           k_col_fwd   column DFTs, reading only the n non-zero rows;
-//           k_degrid    G: Kaiser-Bessel gather of J x J cells per visibility.
-// Adjoint:  k_grid      G^T: per grid tile, shared-memory accumulation of the
-//                       visibilities whose footprint meets the tile (no global
-//                       atomics; each tile is written once);
-//           k_col_inv   inverse column DFTs, keeping the n rows of the image;
-//           k_row_inv   inverse row DFTs, crop Z^T and D, with fused epilogues
-//                       for the CG operator Q = Phi^H Phi + 2I and the SDMM step.
+//           k_col_fwd   column DFTs, reading only the n non-zero rows.
+// Adjoint:  k_col_inv   inverse column DFTs, keeping the n rows of the image;
+//           k_row_inv   inverse row DFTs, crop Z^T, D and B, with fused
+//                       epilogues for the CG operator Q = Phi^H Phi + 2I and
+//                       the SDMM step.
 #include <type_traits>
 
 #include "common.cuh"
@@ -52,13 +50,6 @@ static FftShape col_shape(const purify_ctx* c) {
   f.nsig = nsig;
   f.threads = nsig * c->L / f.ept;
   return f;
-}
-
-// Static plus dynamic shared memory above 48 KB needs a per-kernel opt-in
-// (the kernels' static shared memory is well under 8 KB).
-template <class K>
-static void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,479 +192,6 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
   ColFwdSrc src{half, n, L, c0};
   ColStoreDst dst{X, L, c0};
   fft_fused<EPT, true>(sm, SigLayout{1, nsig}, plan, nsig, sm + nsig * L, tw, src, dst);
-}
-
-// ---------------------------------------------------------------------------
-// Degridding G.  The visibilities are sorted by the grid tile (T x T) holding
-// the first cell of their footprint; one CTA takes a run of one tile's
-// visibilities, stages the (T + J - 1)^2 cells their footprints can reach in
-// shared memory, and gathers J x J cells per visibility from there.
-// ---------------------------------------------------------------------------
-template <int J, int MODE>
-__global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, const float2* __restrict__ uv,
-                                                const int* __restrict__ perm, DegridArgs a,
-                                                const int4* __restrict__ dchunks, KbPoly kb, KappaScale ks, int L,
-                                                int T, int tiles_1d, double* partials, DevScalars* sc) {
-  extern __shared__ float2 halo[];
-  constexpr int NT = 256;
-  const int W = T + J - 1, NW = W * W;
-  const int4 ch = dchunks[blockIdx.x];
-  const int tr = ch.x / tiles_1d, tc = ch.x - tr * tiles_1d;
-  const int R0 = tr * T, C0 = tc * T;
-  // the first frequencies of this thread, in flight with the halo loads
-  constexpr int QV = 4;
-  float2 uq[QV];
-#pragma unroll
-  for (int q = 0; q < QV; ++q) {
-    const int i = ch.y + threadIdx.x + q * NT;
-    if (i < ch.z) uq[q] = __ldg(&uv[i]);
-  }
-  // halo of the tile: eight cells per thread per round, all loads issued first
-  for (int k0 = 0; k0 < NW; k0 += 8 * NT) {
-    float2 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int k = k0 + threadIdx.x + q * NT;
-      if (k < NW) {
-        const int rr = k / W, cc = k - rr * W;  // W = T + J - 1 is not a Div form
-        int r = R0 + rr, c = C0 + cc;
-        if (r >= L) r -= L;
-        if (c >= L) c -= L;
-        v[q] = __ldg(&X[(size_t)r * L + c]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int k = k0 + threadIdx.x + q * NT;
-      if (k < NW) halo[k] = v[q];
-    }
-  }
-  __syncthreads();
-  FPair part[2];  // per-thread exact sums of a few terms; FP64 across threads
-  auto visit = [&](int i, float2 u) {
-    int k0r, k0c;
-    float fr, fc;
-    split_kappa(u.x, ks, k0r, fr);
-    split_kappa(u.y, ks, k0c, fc);
-    k0r -= J / 2 - 1;
-    k0c -= J / 2 - 1;
-    float wr[J], wc[J];
-    kb_weights<J>(kb, fr, wr);
-    kb_weights<J>(kb, fc, wc);
-    const int dr = wrap(k0r - R0, L), dc = wrap(k0c - C0, L);
-    float2 acc = make_float2(0.f, 0.f);
-    if (dr < T && dc < T) {
-      const float2* base = halo + dr * W + dc;
-#pragma unroll
-      for (int aa = 0; aa < J; ++aa) {
-        float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < J; ++b) {
-          const float2 g = base[aa * W + b];
-          t.x = fmaf(wc[b], g.x, t.x);
-          t.y = fmaf(wc[b], g.y, t.y);
-        }
-        acc.x = fmaf(wr[aa], t.x, acc.x);
-        acc.y = fmaf(wr[aa], t.y, acc.y);
-      }
-    } else {
-      // not in this tile (never for a consistent table): read the grid directly
-#pragma unroll
-      for (int aa = 0; aa < J; ++aa) {
-        const float2* row = X + (size_t)wrap(k0r + aa, L) * L;
-        float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < J; ++b) {
-          const float2 g = __ldg(&row[wrap(k0c + b, L)]);
-          t.x = fmaf(wc[b], g.x, t.x);
-          t.y = fmaf(wc[b], g.y, t.y);
-        }
-        acc.x = fmaf(wr[aa], t.x, acc.x);
-        acc.y = fmaf(wr[aa], t.y, acc.y);
-      }
-    }
-    if (MODE == kDegridPerm) {
-      a.out[perm[i]] = acc;
-    } else if (MODE == kDegridSorted) {
-      a.out[i] = acc;
-    } else {
-      // SDMM: s2 = Phi x_hat, and the two FP64 norms of the l2 branch
-      a.out[i] = acc;
-      float2 y;
-      if (a.y) {
-        y = a.y[i];
-      } else {
-        const float sc4 = a.yscale[i >> 12];
-        const uint32_t bits = reinterpret_cast<const uint32_t*>(a.yb)[i];
-        y = make_float2(__uint_as_float(bits << 16) * sc4, __uint_as_float(bits & 0xffff0000u) * sc4);
-      }
-      const float2 z = a.z2[i];
-      const float2 av = cadd(acc, z);
-      part[0].add_sq_diff(av.x, y.x);
-      part[0].add_sq_diff(av.y, y.y);
-      part[1].add_sq_diff(acc.x, y.x);
-      part[1].add_sq_diff(acc.y, y.y);
-    }
-  };
-#pragma unroll
-  for (int q = 0; q < QV; ++q) {
-    const int i = ch.y + threadIdx.x + q * NT;
-    if (i < ch.z) visit(i, uq[q]);
-  }
-  for (int i = ch.y + threadIdx.x + QV * NT; i < ch.z; i += NT) visit(i, __ldg(&uv[i]));
-  if (MODE == kDegridSdmm) {
-    double acc2[2] = {part[0].value(), part[1].value()};
-    double tot[2];
-    if (reduce_last_block<2>(acc2, partials + kCntL2 * 2 * kMaxPartials, &sc->counter[kCntL2], tot)) {
-      sc->l2_dn2 = tot[0];
-      sc->l2_res2 = tot[1];
-      sc->nu = sqrt(tot[1]) / sc->eps;
-      sc->nu_min = sc->nu;
-      const double nd = sqrt(tot[0]);
-      sc->l2_scale = (nd > sc->eps) ? sc->eps / nd : 1.0;  // projection factor of the l2 ball
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Gridding G^T, as a gather (no atomics).  The grid is cut into T x T tiles;
-// set-up listed, per tile, the visibilities whose footprint meets it, sorted
-// by the footprint's first cell relative to the tile (one run per start
-// cell), and cut each list into chunks.  One CTA per chunk stages its
-// entries (start cell, value, J + J kernel weights) in shared memory.  A
-// 2 x 2 block of cells ("owner") sums, in a fixed order, the entries of the
-// (J + 1)^2 start cells whose footprint reaches it: J + 1 runs of the sorted
-// list, one per start row.  The owners' work is uneven (dense start cells
-// where tracks cross), so the CTA splits the concatenation of all owners'
-// runs into equal slices, one per thread (merge-path style): a thread writes
-// the owners that lie inside its slice and leaves two partial sums for the
-// owners cut by its slice ends, which are added afterwards in slice order.
-// A tile with one chunk is written to X directly; otherwise each chunk
-// stores a partial tile and the last chunk to finish adds the partials in
-// chunk order.  Every cell is written once and the result does not depend
-// on scheduling.
-// ---------------------------------------------------------------------------
-// Exclusive prefix sum of one int per thread over the block (blockDim a
-// multiple of 32); *total gets the block sum.
-__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int x = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += t;
-    }
-    if (lane < nw) wsum[lane] = x;  // inclusive warp totals
-  }
-  __syncthreads();
-  const int excl = incl - v + (wid > 0 ? wsum[wid - 1] : 0);
-  *total = wsum[nw - 1];
-  __syncthreads();
-  return excl;
-}
-
-struct Acc4 {  // a 2 x 2 block of complex sums
-  float2 a00, a01, a10, a11;
-};
-
-template <int J, int MODE>
-__global__ void __launch_bounds__(kGridThreads, 3) k_grid(float2* __restrict__ X, const float2* __restrict__ Xin,
-                                                       const int* __restrict__ perm, const float2* __restrict__ vis,
-                                                       const int4* __restrict__ list,
-                                                       const int4* __restrict__ chunks,
-                                                       const int* __restrict__ tile_slot0,
-                                                       const int* __restrict__ tile_nchunk,
-                                                       unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
-                                                       KbPoly kb, KappaScale ks, int L, int T, int tiles_1d,
-                                                       int chunk_max) {
-  constexpr int NT = kGridThreads;
-  constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
-  extern __shared__ float4 sm4[];
-  __shared__ bool s_last;
-  __shared__ int wsum[NT / 32];
-  const int W = T + J - 1, NK = W * W, HB = T / 2, NO = HB * HB;
-  const int lhb = __ffs(HB) - 1;  // T is a power of two
-  float4* part = sm4;  // slot j: first[j] at 4j, last[j] at 4j + 2 (Gram form: the halo first)
-  float2* yv = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm4) + grid_slot_bytes(T, J));
-  float* wt = reinterpret_cast<float*>(yv + chunk_max);
-  int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);
-  int* off = key + chunk_max;  // NK + 1 run offsets
-  int* P = off + NK + 1;       // NO + 1 work prefix of the owners
-  const int4 ch = chunks[blockIdx.x];
-  const int tile = ch.x;
-  const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
-  const int R0 = tr * T, C0 = tc * T;
-  const int ne = ch.z - ch.y;
-  // ---- Gram form (G^T G): stage the (T + 2J - 2)^2 grid cells that the
-  // footprints of the tile's entries cover; each entry's value is then its
-  // degridded sample, in the same order of operations as k_degrid
-  const int HW = T + 2 * (J - 1);
-  float2* halo = reinterpret_cast<float2*>(sm4);
-  if constexpr (MODE == kGridGram) {
-    for (int k0 = 0; k0 < HW * HW; k0 += 8 * NT) {
-      float2 v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + threadIdx.x + q * NT;
-        if (k < HW * HW) {
-          const int rr = k / HW, cc = k - rr * HW;
-          int r = R0 - (J - 1) + rr, c = C0 - (J - 1) + cc;
-          if (r < 0) r += L;
-          if (r >= L) r -= L;
-          if (c < 0) c += L;
-          if (c >= L) c -= L;
-          v[q] = __ldg(&Xin[(size_t)r * L + c]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + threadIdx.x + q * NT;
-        if (k < HW * HW) halo[k] = v[q];
-      }
-    }
-    __syncthreads();
-  }
-  // ---- stage the chunk's entries (loads of four entries per thread in flight)
-  for (int e0 = 0; e0 < ne; e0 += 4 * NT) {
-    int4 le[4];
-    float2 val[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + threadIdx.x + q * NT;
-      le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
-    }
-    if constexpr (MODE != kGridGram) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (le[q].x >= 0) val[q] = (MODE == kGridPerm) ? __ldg(&vis[__ldg(&perm[le[q].x])]) : __ldg(&vis[le[q].x]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (le[q].x < 0) continue;
-      const int e = e0 + threadIdx.x + q * NT;
-      float wr[J], wc[J];
-      kb_weights<J>(kb, __int_as_float(le[q].z), wr);
-      kb_weights<J>(kb, __int_as_float(le[q].w), wc);
-      if constexpr (MODE == kGridGram) {
-        const int kr = le[q].y / W, kc = le[q].y - kr * W;  // footprint start in the halo
-        const float2* base = halo + kr * HW + kc;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int aa = 0; aa < J; ++aa) {
-          float2 t = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int b = 0; b < J; ++b) {
-            const float2 g = base[aa * HW + b];
-            t.x = fmaf(wc[b], g.x, t.x);
-            t.y = fmaf(wc[b], g.y, t.y);
-          }
-          acc.x = fmaf(wr[aa], t.x, acc.x);
-          acc.y = fmaf(wr[aa], t.y, acc.y);
-        }
-        val[q] = acc;
-      }
-      key[e] = le[q].y;
-      yv[e] = val[q];
-      float* w = wt + (size_t)e * S;
-      w[0] = 0.f;
-      w[J + 1] = 0.f;
-      w[J + 2] = 0.f;
-      w[2 * J + 3] = 0.f;
-#pragma unroll
-      for (int k = 0; k < J; ++k) {
-        w[1 + k] = wr[k];
-        w[J + 3 + k] = wc[k];
-      }
-    }
-  }
-  __syncthreads();
-  // ---- off[k] = first entry with key >= k (keys are sorted): binary searches,
-  // each thread a contiguous run of keys
-  {
-    const int per = (NK + 1 + NT - 1) / NT;
-    const int k0 = threadIdx.x * per, k1 = min(k0 + per, NK + 1);
-    int lo = 0;
-    for (int k = k0; k < k1; ++k) {
-      int hi = ne;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (key[mid] < k) lo = mid + 1;
-        else hi = mid;
-      }
-      off[k] = lo;
-    }
-  }
-  __syncthreads();
-  // ---- work of each owner (entries over its J + 1 runs), prefix over owners
-  int Wt;
-  {
-    constexpr int kMaxPer = 4;  // owners per thread: (T / 2)^2 / 256 <= 4 for T <= 64
-    const int per = (NO + NT - 1) / NT;
-    const int o0 = threadIdx.x * per;
-    int cnt[kMaxPer];
-    int run = 0;
-#pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) {
-      const int o = o0 + q;
-      cnt[q] = 0;
-      if (q < per && o < NO) {
-        const int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
-        for (int kr = R; kr <= R + J; ++kr) cnt[q] += off[kr * W + C + J + 1] - off[kr * W + C];
-      }
-      run += cnt[q];
-    }
-    int base = block_excl_scan(run, wsum, &Wt);
-#pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) {
-      const int o = o0 + q;
-      if (q < per && o < NO) {
-        P[o] = base;
-        base += cnt[q];
-      }
-    }
-    if (threadIdx.x == 0) P[NO] = Wt;
-  }
-  __syncthreads();
-  const bool multi = ch.w >= 0;
-  float2* dst = multi ? slots + (size_t)ch.w * T * T : nullptr;
-  auto write_owner = [&](int o, const Acc4& a) {
-    const int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
-    if (!multi) {
-      float2* row0 = X + (size_t)(R0 + R) * L + C0 + C;
-      reinterpret_cast<float4*>(row0)[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
-      reinterpret_cast<float4*>(row0 + L)[0] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
-    } else {
-      reinterpret_cast<float4*>(dst + R * T + C)[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
-      reinterpret_cast<float4*>(dst + (R + 1) * T + C)[0] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
-    }
-  };
-  // ---- this thread's slice [t0, t1) of the concatenated runs, walked as one
-  // flat loop (one entry per step) so the lanes of a warp stay in step
-  const int j = threadIdx.x;
-  const int t0 = (j * Wt + NT - 1) / NT, t1 = ((j + 1) * Wt + NT - 1) / NT;
-  const int nmy = t1 - t0;
-  if (nmy > 0) {
-    int o = 0;  // owner holding t0: the last o with P[o] <= t0
-    {
-      int hi = NO - 1;
-      while (o < hi) {
-        const int mid = (o + hi + 1) >> 1;
-        if (P[mid] <= t0) o = mid;
-        else hi = mid - 1;
-      }
-    }
-    int Po = P[o], Pe = P[o + 1];
-    int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
-    int kr = R, ee = 0, run_end = 0;
-    for (int local = t0 - Po;; ++kr) {  // the run of o holding t0
-      const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
-      if (local < s1 - s0) {
-        ee = s0 + local;
-        run_end = s1;
-        break;
-      }
-      local -= s1 - s0;
-    }
-    int a0 = R + J - 1 - kr, kbase = kr * W;  // row taps of cell rows R, R + 1: padded index a0 + 1, a0 + 2
-    Acc4 a;
-    a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
-    auto flush = [&]() {
-      if (Po >= t0 && Pe <= t1) {
-        write_owner(o, a);
-      } else {
-        float4* sl = part + 4 * j + (Po < t0 ? 0 : 2);  // first / last owner of the slice
-        sl[0] = make_float4(a.a00.x, a.a00.y, a.a01.x, a.a01.y);
-        sl[1] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
-      }
-    };
-    for (int step = 0; step < nmy; ++step) {
-      const int b0 = C + J - 1 - (key[ee] - kbase);  // column tap of cell column C, in [-1, J - 1]
-      const float2 v = yv[ee];
-      const float* w = wt + ee * S;
-      const float wr0 = w[a0 + 1], wr1 = w[a0 + 2];
-      const float wc0 = w[J + 3 + b0], wc1 = w[J + 4 + b0];
-      const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
-      a.a00.x = fmaf(wc0, v0.x, a.a00.x); a.a00.y = fmaf(wc0, v0.y, a.a00.y);
-      a.a01.x = fmaf(wc1, v0.x, a.a01.x); a.a01.y = fmaf(wc1, v0.y, a.a01.y);
-      a.a10.x = fmaf(wc0, v1.x, a.a10.x); a.a10.y = fmaf(wc0, v1.y, a.a10.y);
-      a.a11.x = fmaf(wc1, v1.x, a.a11.x); a.a11.y = fmaf(wc1, v1.y, a.a11.y);
-      if (++ee == run_end && step + 1 < nmy) {
-        // next non-empty run of this owner, else the next owner with work
-        for (;;) {
-          if (++kr > R + J) {
-            flush();
-            a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
-            do {
-              ++o;
-              Po = Pe;
-              Pe = P[o + 1];
-            } while (Pe == Po);
-            R = 2 * (o >> lhb);
-            C = 2 * (o & (HB - 1));
-            kr = R;
-          }
-          const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
-          if (s1 > s0) {
-            ee = s0;
-            run_end = s1;
-            break;
-          }
-        }
-        a0 = R + J - 1 - kr;
-        kbase = kr * W;
-      }
-    }
-    flush();
-  }
-  __syncthreads();
-  // ---- owners cut by slice ends (sum in slice order) and owners with no work
-  for (int o = threadIdx.x; o < NO; o += NT) {
-    const int Po = P[o], Pe = P[o + 1];
-    Acc4 a;
-    a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
-    if (Pe > Po) {
-      const int ja = (Po * NT) / Wt, jb = ((Pe - 1) * NT) / Wt;
-      if (ja == jb) continue;  // written by its slice
-      float4 p0 = part[4 * ja + 2], p1 = part[4 * ja + 3];
-      for (int jj = ja + 1; jj <= jb; ++jj) {
-        if ((jj * Wt + NT - 1) / NT == ((jj + 1) * Wt + NT - 1) / NT) continue;  // empty slice
-        const float4 q0 = part[4 * jj], q1 = part[4 * jj + 1];
-        p0 = make_float4(p0.x + q0.x, p0.y + q0.y, p0.z + q0.z, p0.w + q0.w);
-        p1 = make_float4(p1.x + q1.x, p1.y + q1.y, p1.z + q1.z, p1.w + q1.w);
-      }
-      a.a00 = make_float2(p0.x, p0.y);
-      a.a01 = make_float2(p0.z, p0.w);
-      a.a10 = make_float2(p1.x, p1.y);
-      a.a11 = make_float2(p1.z, p1.w);
-    }
-    write_owner(o, a);
-  }
-  if (!multi) return;
-  __threadfence();
-  __syncthreads();
-  const int nc = tile_nchunk[tile];
-  if (threadIdx.x == 0) s_last = (atomicAdd(&tile_cnt[tile], 1u) == (unsigned)(nc - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int TT = T * T;
-  const float2* first = slots + (size_t)tile_slot0[tile] * TT;
-  for (int k = threadIdx.x; k < TT; k += NT) {
-    float2 sum = make_float2(0.f, 0.f);
-    for (int c = 0; c < nc; ++c) sum = cadd(sum, __ldcg(&first[(size_t)c * TT + k]));
-    const int rr = k / T, cc = k - rr * T;
-    X[(size_t)(R0 + rr) * L + C0 + cc] = sum;
-  }
-  if (threadIdx.x == 0) tile_cnt[tile] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -871,69 +389,6 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
   return check_cuda(cudaGetLastError());
 }
 
-template <int J>
-static void degrid_J(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
-  const int threads = 256;
-  const int W = c->tileT + J - 1;
-  const size_t sm = (size_t)W * W * sizeof(float2);
-#define DEG(MD)                                                                                               \
-  do {                                                                                                        \
-    allow_smem(k_degrid<J, MD>, sm);                                                                          \
-    PURIFY_LAUNCH(c, "degrid", s,                                                                             \
-                  (k_degrid<J, MD><<<c->ndchunks, threads, sm, s>>>(c->d_grid, c->d_uv, c->d_perm, a, c->d_dchunks, \
-                                                                    c->kb, c->ks, c->L, c->tileT, c->tiles_1d,     \
-                                                                    c->d_partials, c->d_sc)));                     \
-  } while (0)
-  if (mode == kDegridPerm) DEG(kDegridPerm);
-  else if (mode == kDegridSorted) DEG(kDegridSorted);
-  else DEG(kDegridSdmm);
-#undef DEG
-}
-
-int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s) {
-  switch (c->J) {
-    case 2: degrid_J<2>(c, mode, a, s); break;
-    case 4: degrid_J<4>(c, mode, a, s); break;
-    case 6: degrid_J<6>(c, mode, a, s); break;
-    default: degrid_J<8>(c, mode, a, s); break;
-  }
-  return check_cuda(cudaGetLastError());
-}
-
-template <int J>
-static size_t grid_smem(const purify_ctx* c) {
-  return grid_fixed_bytes(c->tileT, J) + (size_t)c->chunk_max * grid_entry_bytes(J);
-}
-
-template <int J>
-static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
-  const size_t sm = grid_smem<J>(c);
-#define GRD(MD, NAME, OUT, IN)                                                                                 \
-  do {                                                                                                         \
-    allow_smem(k_grid<J, MD>, sm);                                                                             \
-    PURIFY_LAUNCH(c, NAME, s,                                                                                  \
-                  (k_grid<J, MD><<<c->nchunks, kGridThreads, sm, s>>>(                                         \
-                      OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
-                      c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max)));   \
-  } while (0)
-  if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
-  else if (mode == kGridSorted) GRD(kGridSorted, "grid", c->d_grid, nullptr);
-  else GRD(kGridGram, "gram", c->d_grid2, c->d_grid);
-#undef GRD
-}
-
-// G^T G of the grid in d_grid into d_grid2 (one pass; the M samples are not stored).
-int gram_grid(purify_ctx* c, cudaStream_t s) { return grid_adjoint(c, kGridGram, nullptr, s); }
-
-int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
-  switch (c->J) {
-    case 2: grid_J<2>(c, mode, vis, s); break;
-    case 4: grid_J<4>(c, mode, vis, s); break;
-    case 6: grid_J<6>(c, mode, vis, s); break;
-    default: grid_J<8>(c, mode, vis, s); break;
-  }
-  return check_cuda(cudaGetLastError());
-}
 
 int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* grid) {
   const float* beam = c->beam_on ? c->d_beam : nullptr;

@@ -64,12 +64,12 @@ def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
     prof.mkdir()
     csrc = tmp_path / "paper_1307_4370_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "nufft.cu").write_text("kernel v1\n")
+    (csrc / "gridding.cu").write_text("kernel v1\n")
     sha = hashlib.sha256(b"kernel v1\n").hexdigest()
     (prof / "dram_traffic.txt").write_text(f"# comment\nsdmm256 grid 1234 {sha}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.dram_traffic("sdmm256", "grid") == 1234
     assert bench.dram_traffic("sdmm1024", "grid") is None
     assert bench.dram_traffic("sdmm256", "nosuch") is None
-    (csrc / "nufft.cu").write_text("kernel v2\n")
+    (csrc / "gridding.cu").write_text("kernel v2\n")
     assert bench.dram_traffic("sdmm256", "grid") is None
