@@ -434,7 +434,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
 // update of the previous step (not before the first step), w = Q r, and the
 // step sizes from <r, r> and <w, r> (Chronopoulos & Gear 1989; in exact
 // arithmetic the iterates are those of the standard CG of the x-update).
-int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, float2* w, bool first, cudaStream_t s) {
+int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, float2* w, int i, cudaStream_t s) {
   RowInArgs ia{};
   ia.in = r;
   ia.x = x;
@@ -442,12 +442,13 @@ int cg_step(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, float2* 
   ia.p = p;
   ia.s = sv;
   ia.w = w;
-  TRY(phi_forward_grid(c, first ? kRowInPlain : kRowInCgUpd, ia, s));
+  TRY(phi_forward_grid(c, i == 0 ? kRowInPlain : kRowInCgUpd, ia, s, i - 1));  // applies step i - 1's update
   TRY(gram_grid(c, s));  // G^T G in one pass (the M samples are not stored)
   RowOutArgs ra{};
   ra.out = w;
   ra.p = r;
-  return phi_adjoint_image(c, kRowOutCgQ, ra, s, c->d_grid2);
+  TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s, c->d_grid2));
+  return cg_consumer_blocks(c) > 0 ? PURIFY_OK : launch_cg_scalars(c, i, s);
 }
 
 int64_t ctx_N(const purify_ctx* c) { return (int64_t)c->n * c->n; }
@@ -471,7 +472,7 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   const unsigned long long l0 = g_launches.load(std::memory_order_relaxed);
   // step 5: x_hat = Q^{-1} sum_i x_i by warm-started CG (r holds r0 = b - Q x_hat(t-1))
   const int k = st->params.cg_iters;
-  for (int i = 0; i < k; ++i) TRY(cg_step(c, st->xhat, st->r, st->p, st->sv, st->qp, i == 0, s));
+  for (int i = 0; i < k; ++i) TRY(cg_step(c, st->xhat, st->r, st->p, st->sv, st->qp, i, s));
   // i = 2, first half: s2 = Phi x_hat (after the last CG update) and the l2 norms (FP64)
   RowInArgs ia{};
   ia.in = st->xhat;
@@ -480,7 +481,7 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   ia.p = st->p;
   ia.s = st->sv;
   ia.w = st->qp;
-  TRY(phi_forward_grid(c, k > 0 ? kRowInCgFinish : kRowInPlain, ia, s));
+  TRY(phi_forward_grid(c, k > 0 ? kRowInCgFinish : kRowInPlain, ia, s, k - 1));
   DegridArgs da{};
   da.out = st->s2;
   da.z2 = st->z2;
@@ -761,8 +762,8 @@ int purify_cg_solve(purify_ctx* c, const float* b, float* x, int32_t iters, doub
   ra.p = X;
   TRY(phi_adjoint_image(c, kRowOutCgQ, ra, s));
   TRY(launch_cg_residual_init(c, (const float2*)b, w, r, s));
-  for (int k = 0; k < iters; ++k) TRY(cg_step(c, X, r, p, sv, w, k == 0, s));
-  if (iters > 0) TRY(launch_cg_apply(c, X, r, p, sv, w, s));
+  for (int k = 0; k < iters; ++k) TRY(cg_step(c, X, r, p, sv, w, k, s));
+  if (iters > 0) TRY(launch_cg_apply(c, X, r, p, sv, w, iters - 1, s));
   if (resid_out) TRY_CUDA(cudaMemcpyAsync(resid_out, &c->d_sc->cg_res, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return PURIFY_OK;
 }
@@ -863,7 +864,6 @@ int purify_sdmm_init(purify_ctx* c, purify_sdmm_state* st, const float* y, doubl
   // scalars: everything zero but eps
   DevScalars z{};
   z.eps = eps;
-  z.cg_first = 1;
   std::memcpy(c->h_sc, &z, sizeof(z));
   TRY_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
   // gamma = beta ||Psi^H Phi^H y||_inf (§4.4), via Phi^H y (sorted) into x1 and Psi^H into u1

@@ -172,8 +172,9 @@ struct DevScalars {
   double nu_min;     // smallest block's nu (= nu for one ball)
   double iters;
   double cg_res;
-  int cg_first;      // the next Q-epilogue starts a CG solve
-  int upd_first;     // the pending CG update is the first of a solve (p = r, s = w)
+  double cg_rho[2];   // gamma and alpha of CG steps j - 1 and j, by parity of j
+  double cg_alpha[2];
+  int cg_step_first;  // the step sizes in alpha, beta are those of a first step
   unsigned int counter[kNumCounters];
 };
 
@@ -402,7 +403,15 @@ struct RowOutArgs {
   float2* z3;           // sdmm
 };
 
-int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s);
+// cg_j: in the CG modes, the CG step whose update this pass applies (its
+// inner-product partials are in the kCntDot slot).
+int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j = 0);
+int cg_partial_blocks(const purify_ctx* c);
+// CG step sizes formed by the consuming kernels (few partials) or by a
+// one-block kernel after the inverse row pass (many partials).
+constexpr int kCgConsumeMaxBlocks = 256;
+int cg_consumer_blocks(const purify_ctx* c);  // nblk for the consumers: the partial count, or 0
+int launch_cg_scalars(purify_ctx* c, int cg_j, cudaStream_t s);
 int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s);
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s);
 int gram_grid(purify_ctx* c, cudaStream_t s);
@@ -428,7 +437,8 @@ int launch_l2_norm_diff(purify_ctx* c, int64_t count, const float2* a, const flo
 int launch_l2_project(int64_t count, const float2* in, const float2* y, double eps,
                       const double* norm2_dev, float2* out, cudaStream_t s);
 int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s);
-int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, cudaStream_t s);
+int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, int cg_j,
+                    cudaStream_t s);
 int launch_cg_residual_init(purify_ctx* c, const float2* b, const float2* qx, float2* r, cudaStream_t s);
 int launch_max_abs(purify_ctx* c, int64_t count, const float2* a, cudaStream_t s);
 int launch_sdmm_l2_update(purify_sdmm_state* st, cudaStream_t s);

@@ -158,14 +158,16 @@ __device__ __forceinline__ void fft_smem(float2* buf, SigLayout lay, const FftPl
 // issues all of its global loads (inputs and twiddles) before it uses any of
 // them.
 //
-//   Src: typename Raw; Raw fetch(s, e) const;  float2 prep(const Raw&, s, e) const
+//   Src: typename Raw; Raw fetch(s, e) const;  void between();  float2 prep(const Raw&, s, e) const
 //   Dst: typename Aux; Aux fetch(s, e) const;  void put(s, e, float2, const Aux&)
-// (s = signal, e = element; Dst::fetch runs before the last stage's arithmetic
-// so the epilogue operands are in flight meanwhile.)
+// (s = signal, e = element; Src::between runs in every thread after the first
+// stage's loads are issued, for block-wide work they can overlap; Dst::fetch
+// runs before the last stage's arithmetic so the epilogue operands are in
+// flight meanwhile.)
 // ---------------------------------------------------------------------------
 template <int R, int EPT, bool SIG_FAST, class Src>
 __device__ __forceinline__ void stage_first(float2* buf, SigLayout lay, const Div& lr, const Div& dsig, int nsig,
-                                            const Src& src, float2* tws, const float2 (&twr)[EPT], int L) {
+                                            Src& src, float2* tws, const float2 (&twr)[EPT], int L) {
   constexpr int NB = EPT / R;
   const int LR = lr.d;
   const int nbfly = nsig * LR;
@@ -189,6 +191,7 @@ __device__ __forceinline__ void stage_first(float2* buf, SigLayout lay, const Di
     const int i = threadIdx.x + k * blockDim.x;
     if (i < L) tws[i] = twr[k];
   }
+  src.between();  // block-wide work that overlaps the loads in flight (all threads)
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     const int b = threadIdx.x + k * blockDim.x;
@@ -247,7 +250,7 @@ __device__ __forceinline__ void stage_last(const float2* buf, SigLayout lay, con
 // the L twiddles exp(-2 pi i t / L) copied from `tw`.
 template <int EPT, bool SIG_FAST, class Src, class Dst>
 __device__ __forceinline__ void fft_fused(float2* buf, SigLayout lay, const FftPlan& plan, int nsig, float2* tws,
-                                          const float2* __restrict__ tw, const Src& src, Dst& dst) {
+                                          const float2* __restrict__ tw, Src& src, Dst& dst) {
   const Div dsig = make_div(nsig);
   const int L = plan.L;
   float2 twr[EPT];

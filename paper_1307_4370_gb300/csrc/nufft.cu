@@ -81,6 +81,11 @@ struct RowFwdSrc {
   int n, L, r0;
   float invL, alpha, beta;
   bool first;
+  // CG modes: inner-product partials of the previous CG step j
+  const double* cgpart;
+  int cg_nblk, cg_j;
+  DevScalars* sc;
+  __device__ __forceinline__ void between() {}
   __device__ __forceinline__ Raw fetch(int s, int e) const {
     Raw o;
     const int row = r0 + s;
@@ -137,7 +142,8 @@ struct RowStoreDst {  // row-major rows of length L
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(256) k_row_fwd(RowInArgs a, float2* __restrict__ half, const float* __restrict__ dz,
                                                  const float* __restrict__ beam, const float2* __restrict__ tw,
-                                                 FftPlan plan, int n, int nsig, const DevScalars* __restrict__ sc) {
+                                                 FftPlan plan, int n, int nsig, DevScalars* sc,
+                                                 const double* __restrict__ cgpart, int cg_nblk, int cg_j) {
   extern __shared__ float2 sm[];
   const int L = plan.L;
   RowFwdSrc<MODE> src;
@@ -150,10 +156,17 @@ __global__ void __launch_bounds__(256) k_row_fwd(RowInArgs a, float2* __restrict
   src.invL = 1.0f / (float)L;
   src.alpha = src.beta = 0.f;
   src.first = false;
-  if (MODE != kRowInPlain) {
-    src.alpha = (float)sc->alpha;
-    src.beta = (float)sc->beta;
-    src.first = sc->upd_first != 0;
+  src.cgpart = cgpart;
+  src.cg_nblk = cg_nblk;
+  src.cg_j = cg_j;
+  src.sc = sc;
+  if constexpr (MODE != kRowInPlain) {
+    // step sizes of the pending update, before any data load is in flight
+    // (overlapping them costs registers, hence occupancy, in this pass)
+    const CgStep st = cg_consume(cgpart, cg_nblk, cg_j, sc);
+    src.alpha = st.alpha;
+    src.beta = st.beta;
+    src.first = st.first;
   }
   RowStoreDst dst{half + (size_t)src.r0 * L, L};
   fft_fused<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, sm + nsig * L, tw, src, dst);
@@ -165,6 +178,7 @@ __global__ void __launch_bounds__(256) k_row_fwd(RowInArgs a, float2* __restrict
 // ---------------------------------------------------------------------------
 struct ColFwdSrc {
   using Raw = float2;
+  __device__ __forceinline__ void between() {}
   const float2* half;
   int n, L, c0;
   __device__ __forceinline__ Raw fetch(int s, int e) const {
@@ -200,6 +214,7 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const float2* __restrict__ hal
 // ---------------------------------------------------------------------------
 struct ColInvSrc {
   using Raw = float2;
+  __device__ __forceinline__ void between() {}
   const float2* X;
   int L, c0;
   __device__ __forceinline__ Raw fetch(int s, int e) const { return X[(size_t)e * L + c0 + s]; }
@@ -241,6 +256,7 @@ __global__ void __launch_bounds__(1024) k_col_inv(const float2* __restrict__ X, 
 // ---------------------------------------------------------------------------
 struct RowInvSrc {
   using Raw = float2;
+  __device__ __forceinline__ void between() {}
   const float2* half;
   int L, r0;
   __device__ __forceinline__ Raw fetch(int s, int e) const { return half[(size_t)(r0 + s) * L + e]; }
@@ -327,32 +343,46 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half
   dst.invL = 1.0f / (float)L;
   fft_fused<EPT, false>(sm, SigLayout{L, 1}, plan, nsig, sm + nsig * L, tw, src, dst);
   if (MODE == kRowOutCgQ) {
+    // per-block partials of gamma = <r, r> and delta = <Qr, r>; the kernel
+    // that applies this step's update adds them and forms the step sizes
     double acc[2] = {dst.part[0].value(), dst.part[1].value()};
-    double tot[2];
-    if (reduce_last_block<2>(acc, partials + kCntDot * 2 * kMaxPartials, &sc->counter[kCntDot], tot)) {
-      const double gamma = tot[0], delta = tot[1];
-      const bool first = sc->cg_first != 0 || sc->alpha == 0.0 || sc->rho == 0.0;
-      const double beta = first ? 0.0 : gamma / sc->rho;
-      const double den = first ? delta : delta - beta * gamma / sc->alpha;
-      sc->pqp = den;
-      sc->beta = beta;
-      sc->alpha = den > 0.0 ? gamma / den : 0.0;
-      sc->rho = gamma;
-      sc->cg_res = sqrt(gamma);
-      sc->upd_first = first ? 1 : 0;
-      sc->cg_first = 0;
+    block_reduce<2>(acc);
+    if (threadIdx.x == 0) {
+      partials[kCntDot * 2 * kMaxPartials + blockIdx.x] = acc[0];
+      partials[kCntDot * 2 * kMaxPartials + kMaxPartials + blockIdx.x] = acc[1];
     }
-  } else if (MODE == kRowOutSdmm) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_first = 1;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s) {
+// Blocks of the inverse row pass, i.e. the CG inner-product partials it leaves.
+int cg_partial_blocks(const purify_ctx* c) { return c->n / row_shape(c).nsig; }
+
+int cg_consumer_blocks(const purify_ctx* c) {
+  const int nb = cg_partial_blocks(c);
+  return nb <= kCgConsumeMaxBlocks ? nb : 0;
+}
+
+// One block: the step sizes of CG step j from the partials, for consumers
+// that read them (cg_consumer_blocks == 0).
+__global__ void __launch_bounds__(256) k_cg_scalars(const double* __restrict__ part, int nblk, int j, DevScalars* sc) {
+  cg_consume(part, nblk, j, sc);
+}
+
+int launch_cg_scalars(purify_ctx* c, int cg_j, cudaStream_t s) {
+  PURIFY_LAUNCH(c, "cg_scalars", s,
+                (k_cg_scalars<<<1, 256, 0, s>>>(c->d_partials + kCntDot * 2 * kMaxPartials, cg_partial_blocks(c), cg_j,
+                                               c->d_sc)));
+  return check_cuda(cudaGetLastError());
+}
+
+int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j) {
   const float* beam = c->beam_on ? c->d_beam : nullptr;
   const FftShape rs = row_shape(c), cs = col_shape(c);
+  const double* cgpart = c->d_partials + kCntDot * 2 * kMaxPartials;
+  const int cg_nblk = cg_consumer_blocks(c);
   const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
   const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);
   const int gr = c->n / rs.nsig, gc = c->L / cs.nsig;
@@ -361,7 +391,7 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
     allow_smem(k_row_fwd<E, MD>, smr);                                                                     \
     PURIFY_LAUNCH(c, "row_fwd", s,                                                                         \
                   (k_row_fwd<E, MD><<<gr, rs.threads, smr, s>>>(a, c->d_half, c->d_deapod, beam, c->d_tw, c->plan, \
-                                                                c->n, rs.nsig, c->d_sc)));                   \
+                                                                c->n, rs.nsig, c->d_sc, cgpart, cg_nblk, cg_j)));   \
   } while (0)
   if (rs.ept == 8) {
     if (mode == kRowInPlain) ROWF(8, kRowInPlain);

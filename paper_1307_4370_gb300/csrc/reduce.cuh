@@ -121,4 +121,62 @@ __device__ __forceinline__ bool reduce_last_block(double* v, double* partials, u
   return threadIdx.x == 0;
 }
 
+// ---------------------------------------------------------------------------
+// Step sizes of single-reduction CG (Chronopoulos & Gear 1989), formed by the
+// kernel that applies the update rather than by a last block of the kernel
+// that produced the inner products.  CG step j's Q-epilogue left per-block
+// partials of gamma_j = <r, r> and delta_j = <Qr, r>; every block of the
+// consumer adds them in the same fixed order (so all blocks agree bit for
+// bit) and forms
+//   beta_j  = gamma_j / gamma_{j-1}         (0 for the first step)
+//   alpha_j = gamma_j / (delta_j - beta_j gamma_j / alpha_{j-1}),
+// reading step j-1's (gamma, alpha) from slot (j-1) & 1; block 0 stores step
+// j's in slot j & 1, which no block of this kernel reads.  Every thread of
+// the block calls it; the results are returned to all of them.  With many
+// partials (large images) a one-block kernel forms them once instead
+// (k_cg_scalars) and the consumers pass nblk = 0 to read its result.
+// ---------------------------------------------------------------------------
+struct CgStep {
+  float alpha, beta;
+  bool first;
+};
+
+__device__ __forceinline__ CgStep cg_consume(const double* __restrict__ part, int nblk, int j, DevScalars* sc) {
+  __shared__ float s_al, s_be;
+  __shared__ int s_first;
+  if (nblk == 0) {  // formed by k_cg_scalars for this step (many partials)
+    return CgStep{(float)sc->alpha, (float)sc->beta, sc->cg_step_first != 0};
+  }
+  double v[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    v[0] += __ldcg(&part[i]);
+    v[1] += __ldcg(&part[kMaxPartials + i]);
+  }
+  block_reduce<2>(v);
+  if (threadIdx.x == 0) {
+    const double gamma = v[0], delta = v[1];
+    const int prev = (j - 1) & 1;
+    const double rho_p = j > 0 ? sc->cg_rho[prev] : 0.0, al_p = j > 0 ? sc->cg_alpha[prev] : 0.0;
+    const bool first = j == 0 || al_p == 0.0 || rho_p == 0.0;
+    const double beta = first ? 0.0 : gamma / rho_p;
+    const double den = first ? delta : delta - beta * gamma / al_p;
+    const double alpha = den > 0.0 ? gamma / den : 0.0;
+    s_al = (float)alpha;
+    s_be = (float)beta;
+    s_first = first ? 1 : 0;
+    if (blockIdx.x == 0) {
+      sc->cg_rho[j & 1] = gamma;
+      sc->cg_alpha[j & 1] = alpha;
+      sc->alpha = alpha;
+      sc->beta = beta;
+      sc->rho = gamma;
+      sc->pqp = den;
+      sc->cg_res = sqrt(gamma);
+      sc->cg_step_first = first ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  return CgStep{s_al, s_be, s_first != 0};
+}
+
 }  // namespace purify

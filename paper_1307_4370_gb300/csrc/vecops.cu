@@ -72,9 +72,11 @@ __global__ void k_positive(int64_t n, const float2* __restrict__ in, float2* __r
 // applied by the forward row pass of the next step):
 // p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s.
 __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__ p,
-                           float2* __restrict__ sv, const float2* __restrict__ w, double* partials, DevScalars* sc) {
-  const float al = (float)sc->alpha, be = (float)sc->beta;
-  const bool first = sc->upd_first != 0;
+                           float2* __restrict__ sv, const float2* __restrict__ w, double* partials, DevScalars* sc,
+                           int cg_nblk, int cg_j) {
+  const CgStep cs = cg_consume(partials + kCntDot * 2 * kMaxPartials, cg_nblk, cg_j, sc);
+  const float al = cs.alpha, be = cs.beta;
+  const bool first = cs.first;
   FPair part;
   GRID_STRIDE(j, n) {
     const float2 rr = r[j], ww = w[j];
@@ -99,11 +101,10 @@ __global__ void k_cg_apply(int64_t n, float2* __restrict__ x, float2* __restrict
     sc->cg_res = sqrt(tot);  // recurrence residual after the last update
 }
 
-// r = b - Qx (the start of purify_cg_solve); the next Q-epilogue starts the solve.
+// r = b - Qx (the start of purify_cg_solve).
 __global__ void k_cg_residual_init(int64_t n, const float2* __restrict__ b, const float2* __restrict__ qx,
                                    float2* __restrict__ r, DevScalars* sc) {
   GRID_STRIDE(j, n) r[j] = csub(b[j], qx[j]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->cg_first = 1;
 }
 
 // max |a_j| -> sc->amax
@@ -293,9 +294,11 @@ int launch_positive(int64_t count, const float2* in, float2* out, cudaStream_t s
   return check_cuda(cudaGetLastError());
 }
 
-int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, cudaStream_t s) {
+int launch_cg_apply(purify_ctx* c, float2* x, float2* r, float2* p, float2* sv, const float2* w, int cg_j,
+                    cudaStream_t s) {
   const int64_t N = (int64_t)c->n * c->n;
-  PURIFY_LAUNCH(c, "cg_apply", s, (k_cg_apply<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, sv, w, c->d_partials, c->d_sc)));
+  PURIFY_LAUNCH(c, "cg_apply", s, (k_cg_apply<<<blocks_for(N), 256, 0, s>>>(N, x, r, p, sv, w, c->d_partials, c->d_sc,
+                                                                           cg_consumer_blocks(c), cg_j)));
   return check_cuda(cudaGetLastError());
 }
 
