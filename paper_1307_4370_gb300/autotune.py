@@ -5,8 +5,9 @@ degridding gather and the gridding adjoint: larger tiles duplicate fewer
 footprints across tile edges, smaller tiles give more, lighter work units.
 The best choice depends on the image side n, the number of visibilities M,
 the kernel support J and the GPU, so it is measured: each candidate context
-times Phi + Phi^H with CUDA events and the fastest is kept, cached per
-(device, n, M, J) in a JSON file.  The schedule never changes the operator;
+times the operator mix of one SDMM iteration (Phi + Phi^H and a 10-step CG
+solve, whose G^T G runs in the one-pass Gram form) with CUDA events, and the
+fastest is kept, cached per (device, n, M, J) in a JSON file.  The schedule never changes the operator;
 all candidates compute the same Phi up to floating-point summation order.
 """
 from __future__ import annotations
@@ -68,6 +69,22 @@ def time_phi_pair(ctx: binding.Context, reps: int = 20) -> float:
     return a.elapsed_time(b) / reps
 
 
+def time_cg(ctx: binding.Context, iters: int = 10, reps: int = 5) -> float:
+    """Mean milliseconds of a CG solve of ``iters`` steps on Q = Phi^H Phi + 2I
+    (the x-update of every SDMM iteration; G^T G runs in its one-pass form)."""
+    b = torch.randn(ctx.n, ctx.n, dtype=torch.complex64, device=ctx.device)
+    x0 = torch.zeros_like(b)
+    ctx.cg_solve(b, x0, iters)
+    s = torch.cuda.current_stream()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        ctx.cg_solve(b, x0, iters)
+    e.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(e) / reps
+
+
 def autotune_tile(n: int, uv, J: int, levels: int = 4, bases_mask: int = binding.SARA_MASK,
                   cache_path: str | None = DEFAULT_CACHE, reps: int = 20, refresh: bool = False) -> dict:
     """Pick the tile side for (n, M, J); returns {"tile", "ms", "timings"}."""
@@ -80,7 +97,8 @@ def autotune_tile(n: int, uv, J: int, levels: int = 4, bases_mask: int = binding
     timings = {}
     for t in valid_tiles(n, J):
         ctx = binding.Context(n, uv, J=J, levels=levels, bases_mask=bases_mask, tile=t)
-        timings[str(t)] = time_phi_pair(ctx, reps)
+        # the operator mix of one SDMM iteration: a CG solve (Gram form) plus Phi and Phi^H
+        timings[str(t)] = time_phi_pair(ctx, reps) + time_cg(ctx, 10, max(1, reps // 4))
         ctx.close()
     best = min(timings, key=timings.get)
     entry = {"tile": int(best), "ms": timings[best], "timings": timings}

@@ -361,8 +361,11 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   // kernel's fixed tables, fit a shared-memory budget that keeps three CTAs
   // resident per SM
   const int64_t mean = (c->nlist + c->ntiles - 1) / c->ntiles;
-  const int64_t room = (int64_t)purify::kGridSmemBudget - (int64_t)purify::grid_fixed_bytes(T, J);
-  const int cap = (int)std::max<int64_t>(128, room / (int64_t)purify::grid_entry_bytes(J) / 32 * 32);
+  // (large tiles: room for at least 512 entries beyond the fixed tables, even
+  // if fewer CTAs then fit on an SM)
+  const int64_t fixed = (int64_t)purify::grid_fixed_bytes(T, J), per = (int64_t)purify::grid_entry_bytes(J);
+  const int64_t budget = std::max<int64_t>((int64_t)purify::kGridSmemBudget, fixed + 512 * per);
+  const int cap = (int)std::max<int64_t>(128, (budget - fixed) / per / 32 * 32);
   c->chunk_max = (int)std::min<int64_t>(cap, std::max<int64_t>(256, ((3 * mean / 2 + 127) / 128) * 128));
   std::vector<int4> chunks;
   std::vector<int> slot0(c->ntiles, -1), nchunk(c->ntiles, 0);

@@ -225,6 +225,13 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   // degridded sample, in the same order of operations as k_degrid
   const int HW = T + 2 * (J - 1);
   float2* halo = reinterpret_cast<float2*>(sm4);
+  // the first four list entries of each thread, in flight with the halo loads
+  int4 le[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + q * NT;
+    le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
+  }
   if constexpr (MODE == kGridGram) {
     for (int k0 = 0; k0 < HW * HW; k0 += 8 * NT) {
       float2 v[8];
@@ -251,12 +258,13 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   }
   // ---- stage the chunk's entries (loads of four entries per thread in flight)
   for (int e0 = 0; e0 < ne; e0 += 4 * NT) {
-    int4 le[4];
     float2 val[4];
+    if (e0 > 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = e0 + threadIdx.x + q * NT;
-      le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + threadIdx.x + q * NT;
+        le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
+      }
     }
     if constexpr (MODE != kGridGram) {
 #pragma unroll

@@ -48,6 +48,20 @@ __device__ __forceinline__ void load_filters(const WaveletFilters& wf, int p, fl
 // Soft threshold + dual update for one final coefficient alpha at index j;
 // returns w |alpha| (its term of f1), summed per thread in FP32 (a few terms)
 // and across threads in FP64.
+// The same with z1_j and w_j already loaded.
+__device__ __forceinline__ float sara_prox_v(float2 al, float2 z, float w, size_t j, const SaraProxArgs& pa,
+                                             float gamma) {
+  const float2 a = cadd(al, z);
+  const float mag = sqrtf(a.x * a.x + a.y * a.y);
+  const float shrink = fmaxf(mag - gamma * w, 0.0f);
+  const float s = mag > 0.0f ? shrink / mag : 0.0f;
+  const float2 r1 = cscale(a, s);
+  const float2 z1n = csub(a, r1);
+  pa.z1[j] = z1n;
+  pa.u1[j] = csub(r1, z1n);
+  return w * sqrtf(fmaf(al.x, al.x, al.y * al.y));
+}
+
 __device__ __forceinline__ float sara_prox(float2 al, size_t j, const SaraProxArgs& pa, float gamma) {
   const float w = pa.w ? pa.w[j] : 1.0f;
   const float2 z = pa.z1[j];
@@ -108,14 +122,24 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   load_filters(wf, p, h, g);
   const float2* src = in_shared ? in : in + (size_t)k * (G.n / 2) * (G.n / 2);
   const Div dL = make_div(L), dTI = make_div(TI), d2TI = make_div(2 * TI);
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int rr = threadIdx.x >> 5; rr < RH; rr += nw) {
-    int r = 2 * I1 + rr;
-    r -= udiv(r, dL) * L;
-    for (int cc = lane; cc < RH; cc += 32) {
-      int c = 2 * I2 + cc;
-      c -= udiv(c, dL) * L;
-      inb[rr * RH + cc] = src[(size_t)r * L + c];
+  // input tile with its halo (periodic): eight loads per thread in flight per round
+  for (int k0 = 0; k0 < RH * RH; k0 += 8 * (int)blockDim.x) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = k0 + threadIdx.x + q * blockDim.x;
+      if (e < RH * RH) {
+        const int rr = e / RH, cc = e - rr * RH;
+        int r = 2 * I1 + rr, c = 2 * I2 + cc;
+        r -= udiv(r, dL) * L;
+        c -= udiv(c, dL) * L;
+        v[q] = src[(size_t)r * L + c];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = k0 + threadIdx.x + q * blockDim.x;
+      if (e < RH * RH) inb[e] = v[q];
     }
   }
   __syncthreads();
@@ -138,45 +162,79 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   float2* llk = ll_out + (size_t)k * (G.n / 2) * (G.n / 2);
   const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
   float f1 = 0.f;
-  for (int idx = threadIdx.x; idx < TI * 2 * TI; idx += blockDim.x) {
-    const int i1 = udiv(idx, d2TI), kc = idx - i1 * (2 * TI);
+  // columns of this thread's (at most two, TI <= 16) outputs, then every
+  // output with its prox operands loaded together
+  constexpr int kMaxIdx = 2;  // TI * 2TI / 256
+  float2 lov[kMaxIdx], hiv[kMaxIdx];
+  int idxv[kMaxIdx];
+#pragma unroll
+  for (int t = 0; t < kMaxIdx; ++t) {
+    const int idx = threadIdx.x + t * blockDim.x;
+    idxv[t] = idx < TI * 2 * TI ? idx : -1;
     float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
-    for (int m = 0; m < taps; ++m) {
-      const float2 v = rowp[(2 * i1 + m) * (2 * TI) + kc];
-      lo.x = fmaf(h[m], v.x, lo.x); lo.y = fmaf(h[m], v.y, lo.y);
-      hi.x = fmaf(g[m], v.x, hi.x); hi.y = fmaf(g[m], v.y, hi.y);
+    if (idxv[t] >= 0) {
+      const int i1 = udiv(idx, d2TI), kc = idx - i1 * (2 * TI);
+      for (int m = 0; m < taps; ++m) {
+        const float2 v = rowp[(2 * i1 + m) * (2 * TI) + kc];
+        lo.x = fmaf(h[m], v.x, lo.x); lo.y = fmaf(h[m], v.y, lo.y);
+        hi.x = fmaf(g[m], v.x, hi.x); hi.y = fmaf(g[m], v.y, hi.y);
+      }
     }
+    lov[t] = lo;
+    hiv[t] = hi;
+  }
+  // destinations: LL = lo of a (top-left), LH = lo of d (top-right),
+  // HL = hi of a (bottom-left), HH = hi of d; on coarser levels LL goes to llk
+  size_t jo[2 * kMaxIdx];
+  float2 ao[2 * kMaxIdx];
+  bool to_plane[2 * kMaxIdx];
+#pragma unroll
+  for (int t = 0; t < kMaxIdx; ++t) {
+    jo[2 * t] = jo[2 * t + 1] = 0;
+    to_plane[2 * t] = to_plane[2 * t + 1] = false;
+    ao[2 * t] = ao[2 * t + 1] = make_float2(0.f, 0.f);
+    if (idxv[t] < 0) continue;
+    const int i1 = udiv(idxv[t], d2TI), kc = idxv[t] - i1 * (2 * TI);
     const int gi1 = I1 + i1;
     const bool rowlow = kc < TI;
     const int gi2 = I2 + (rowlow ? kc : kc - TI);
-    // lo: column-low; hi: column-high.  rowlow: the row-low half [a].
-    // LL = lo of a (top-left), LH = lo of d (top-right), HL = hi of a (bottom-left), HH = hi of d.
     if (rowlow) {
       if (G.last) {
-        const size_t j = (size_t)gi1 * G.n + gi2;
-        const float2 al = cscale(lo, G.scale);
-        if (MODE == kSaraPlain) plane[j] = al;
-        else f1 += sara_prox(al, (size_t)(G.plane0 + k) * G.n * G.n + j, pa, gamma);
+        jo[2 * t] = (size_t)gi1 * G.n + gi2;
+        ao[2 * t] = cscale(lov[t], G.scale);
+        to_plane[2 * t] = true;
       } else {
-        llk[(size_t)gi1 * H + gi2] = lo;
+        llk[(size_t)gi1 * H + gi2] = lov[t];
       }
-      const size_t j = (size_t)(H + gi1) * G.n + gi2;  // HL
-      const float2 al = cscale(hi, G.scale);
-      if (MODE == kSaraPlain) plane[j] = al;
-      else f1 += sara_prox(al, (size_t)(G.plane0 + k) * G.n * G.n + j, pa, gamma);
+      jo[2 * t + 1] = (size_t)(H + gi1) * G.n + gi2;  // HL
+      ao[2 * t + 1] = cscale(hiv[t], G.scale);
     } else {
-      const size_t j1 = (size_t)gi1 * G.n + H + gi2;        // LH
-      const size_t j2 = (size_t)(H + gi1) * G.n + H + gi2;  // HH
-      const float2 a1 = cscale(lo, G.scale), a2 = cscale(hi, G.scale);
-      if (MODE == kSaraPlain) {
-        plane[j1] = a1;
-        plane[j2] = a2;
-      } else {
-        const size_t b = (size_t)(G.plane0 + k) * G.n * G.n;
-        f1 += sara_prox(a1, b + j1, pa, gamma);
-        f1 += sara_prox(a2, b + j2, pa, gamma);
+      jo[2 * t] = (size_t)gi1 * G.n + H + gi2;                // LH
+      jo[2 * t + 1] = (size_t)(H + gi1) * G.n + H + gi2;      // HH
+      ao[2 * t] = cscale(lov[t], G.scale);
+      ao[2 * t + 1] = cscale(hiv[t], G.scale);
+      to_plane[2 * t] = true;
+    }
+    to_plane[2 * t + 1] = true;
+  }
+  const size_t pbase = (size_t)(G.plane0 + k) * G.n * G.n;
+  if (MODE == kSaraPlain) {
+#pragma unroll
+    for (int o = 0; o < 2 * kMaxIdx; ++o)
+      if (to_plane[o]) plane[jo[o]] = ao[o];
+  } else {
+    float2 zv[2 * kMaxIdx];
+    float wv[2 * kMaxIdx];
+#pragma unroll
+    for (int o = 0; o < 2 * kMaxIdx; ++o) {
+      if (to_plane[o]) {
+        zv[o] = pa.z1[pbase + jo[o]];
+        wv[o] = pa.w ? pa.w[pbase + jo[o]] : 1.0f;
       }
     }
+#pragma unroll
+    for (int o = 0; o < 2 * kMaxIdx; ++o)
+      if (to_plane[o]) f1 += sara_prox_v(ao[o], zv[o], wv[o], pbase + jo[o], pa, gamma);
   }
   if (MODE == kSaraProx) {
     double f1d = (double)f1, tot;
@@ -212,11 +270,13 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   // the finest level loops over all planes in one CTA; otherwise one plane per z
   const int kbeg = G.last ? 0 : blockIdx.z;
   const int kend = G.last ? G.nb : blockIdx.z + 1;
-  float2 accum[16];  // up to (2TO)^2 / blockDim outputs per thread: 1024 / 256 = 4 (<= 16 for safety)
+  constexpr int kMaxOut = 4;  // (2TO)^2 / blockDim outputs per thread: 1024 / 256
+  float2 accum[kMaxOut];
   const int nout = (2 * TO) * (2 * TO);
   const Div dH = make_div(H), d2TO = make_div(2 * TO);
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = 0; t < 16; ++t) accum[t] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int t = 0; t < kMaxOut; ++t) accum[t] = make_float2(0.f, 0.f);
   for (int k = kbeg; k < kend; ++k) {
     const int p = bl.p[k];
     const int taps = 2 * p;
@@ -234,17 +294,32 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     const int llstride = ll_from_plane ? G.n : H;
     // window origin: coefficient K/2 - p + 1 (mod H)
     const int o1 = K1 / 2 - p + 1 + 8 * H, o2 = K2 / 2 - p + 1 + 8 * H;  // shifted to stay >= 0
-    for (int t1 = threadIdx.x >> 5; t1 < CW; t1 += nw) {
-      int c1 = o1 + t1;
-      c1 -= udiv(c1, dH) * H;
-      for (int t2 = lane; t2 < CW; t2 += 32) {
-        int c2 = o2 + t2;
-        c2 -= udiv(c2, dH) * H;
-        const int idx = t1 * CW + t2;
-        LLs[idx] = llsrc[(size_t)c1 * llstride + c2];
-        HLs[idx] = plane[(size_t)(H + c1) * G.n + c2];
-        LHs[idx] = plane[(size_t)c1 * G.n + H + c2];
-        HHs[idx] = plane[(size_t)(H + c1) * G.n + H + c2];
+    // the four coefficient windows, sixteen loads per thread in flight per round
+    for (int k0 = 0; k0 < CW * CW; k0 += 4 * (int)blockDim.x) {
+      float2 v[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = k0 + threadIdx.x + q * blockDim.x;
+        if (e < CW * CW) {
+          const int t1 = e / CW, t2 = e - t1 * CW;
+          int c1 = o1 + t1, c2 = o2 + t2;
+          c1 -= udiv(c1, dH) * H;
+          c2 -= udiv(c2, dH) * H;
+          v[q][0] = llsrc[(size_t)c1 * llstride + c2];
+          v[q][1] = plane[(size_t)(H + c1) * G.n + c2];
+          v[q][2] = plane[(size_t)c1 * G.n + H + c2];
+          v[q][3] = plane[(size_t)(H + c1) * G.n + H + c2];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = k0 + threadIdx.x + q * blockDim.x;
+        if (e < CW * CW) {
+          LLs[e] = v[q][0];
+          HLs[e] = v[q][1];
+          LHs[e] = v[q][2];
+          HHs[e] = v[q][3];
+        }
       }
     }
     __syncthreads();
@@ -267,8 +342,10 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     }
     __syncthreads();
     // row synthesis
-    int t = 0;
-    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
+#pragma unroll
+    for (int t = 0; t < kMaxOut; ++t) {
+      const int idx = threadIdx.x + t * blockDim.x;
+      if (idx >= nout) continue;
       const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
       float2 s = make_float2(0.f, 0.f);
       for (int m = (k2 & 1); m < taps; m += 2) {
@@ -286,8 +363,10 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     }
   }
   if (G.last) {
-    int t = 0;
-    for (int idx = threadIdx.x; idx < nout; idx += blockDim.x, ++t) {
+#pragma unroll
+    for (int t = 0; t < kMaxOut; ++t) {
+      const int idx = threadIdx.x + t * blockDim.x;
+      if (idx >= nout) continue;
       const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
       const int gk1 = K1 + k1, gk2 = K2 + k2;
       if (gk1 < L && gk2 < L) {
