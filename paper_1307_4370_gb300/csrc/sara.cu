@@ -30,6 +30,8 @@ struct LevelGeom {
   int plane0;   // index of the first wavelet plane in the coefficient array
   int last;     // analysis: last level (LL goes to the plane); synthesis: finest level
   float scale;  // 1 / sqrt(q)
+  int first;    // analysis: first level (its f1 total replaces the previous one)
+  int dirac;    // analysis, first level: plane of the Dirac basis handled by the CTAs with z = nb, or -1
 };
 
 struct BasisList {
@@ -111,6 +113,21 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   __shared__ float h[kMaxTaps], g[kMaxTaps];
   extern __shared__ float2 sm[];
   const int k = blockIdx.z;
+  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
+  float f1 = 0.f;
+  if (k == G.nb) {
+    // the Dirac plane (first level only): alpha_0 = x / sqrt(q) on this CTA's
+    // 2TI x 2TI block of pixels, with its prox update
+    const int TI = G.tile, r0 = 2 * blockIdx.y * TI, c0 = 2 * blockIdx.x * TI;
+    const size_t base = (size_t)G.dirac * G.n * G.n;
+    for (int e = threadIdx.x; e < 4 * TI * TI; e += blockDim.x) {
+      const int rr = e / (2 * TI), cc = e - rr * (2 * TI);
+      const size_t j = (size_t)(r0 + rr) * G.n + c0 + cc;
+      const float2 al = cscale(in[j], G.scale);
+      if (MODE == kSaraPlain) coef[base + j] = al;
+      else f1 += sara_prox(al, base + j, pa, gamma);
+    }
+  } else {
   const int p = bl.p[k];
   const int taps = 2 * p;
   const int L = G.L, H = L / 2;
@@ -160,8 +177,6 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
   // columns, and the write-out of the four sub-bands
   float2* plane = coef + (size_t)(G.plane0 + k) * G.n * G.n;
   float2* llk = ll_out + (size_t)k * (G.n / 2) * (G.n / 2);
-  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
-  float f1 = 0.f;
   // columns of this thread's (at most two, TI <= 16) outputs, then every
   // output with its prox operands loaded together
   constexpr int kMaxIdx = 2;  // TI * 2TI / 256
@@ -236,10 +251,11 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
     for (int o = 0; o < 2 * kMaxIdx; ++o)
       if (to_plane[o]) f1 += sara_prox_v(ao[o], zv[o], wv[o], pbase + jo[o], pa, gamma);
   }
+  }
   if (MODE == kSaraProx) {
     double f1d = (double)f1, tot;
     if (reduce_last_block<1>(&f1d, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot)) {
-      sc->f1 += tot;
+      sc->f1 = G.first ? tot : sc->f1 + tot;
       if (G.last) {
         // halting quantity zeta of §4.4 (after the last contribution)
         const double prev = sc->f1_prev;
@@ -277,6 +293,34 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
   for (int t = 0; t < kMaxOut; ++t) accum[t] = make_float2(0.f, 0.f);
+  // the four coefficient windows of plane kk, loaded into registers (CW^2 <=
+  // 4 blockDim for TO <= 16, p <= 8): plane k + 1's loads are in flight while
+  // plane k is synthesised
+  float2 v[4][4];
+  auto issue = [&](int kk) {
+    const int pk = bl.p[kk];
+    const int CWk = TO + pk - 1;
+    const float2* plk = coef + (size_t)(G.plane0 + kk) * G.n * G.n;
+    const float2* llk = ll_from_plane ? plk : ll_in + (size_t)kk * (G.n / 2) * (G.n / 2);
+    const int lls = ll_from_plane ? G.n : H;
+    // window origin: coefficient K/2 - p + 1 (mod H), shifted to stay >= 0
+    const int o1 = K1 / 2 - pk + 1 + 8 * H, o2 = K2 / 2 - pk + 1 + 8 * H;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < CWk * CWk) {
+        const int t1 = e / CWk, t2 = e - t1 * CWk;
+        int c1 = o1 + t1, c2 = o2 + t2;
+        c1 -= udiv(c1, dH) * H;
+        c2 -= udiv(c2, dH) * H;
+        v[q][0] = llk[(size_t)c1 * lls + c2];
+        v[q][1] = plk[(size_t)(H + c1) * G.n + c2];
+        v[q][2] = plk[(size_t)c1 * G.n + H + c2];
+        v[q][3] = plk[(size_t)(H + c1) * G.n + H + c2];
+      }
+    }
+  };
+  issue(kbeg);
   for (int k = kbeg; k < kend; ++k) {
     const int p = bl.p[k];
     const int taps = 2 * p;
@@ -289,40 +333,18 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     float2* Ds = As + 2 * TO * CW;             // 2TO x CW
     __syncthreads();
     load_filters(wf, p, h, g);
-    const float2* plane = coef + (size_t)(G.plane0 + k) * G.n * G.n;
-    const float2* llsrc = ll_from_plane ? plane : ll_in + (size_t)k * (G.n / 2) * (G.n / 2);
-    const int llstride = ll_from_plane ? G.n : H;
-    // window origin: coefficient K/2 - p + 1 (mod H)
-    const int o1 = K1 / 2 - p + 1 + 8 * H, o2 = K2 / 2 - p + 1 + 8 * H;  // shifted to stay >= 0
-    // the four coefficient windows, sixteen loads per thread in flight per round
-    for (int k0 = 0; k0 < CW * CW; k0 += 4 * (int)blockDim.x) {
-      float2 v[4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = k0 + threadIdx.x + q * blockDim.x;
-        if (e < CW * CW) {
-          const int t1 = e / CW, t2 = e - t1 * CW;
-          int c1 = o1 + t1, c2 = o2 + t2;
-          c1 -= udiv(c1, dH) * H;
-          c2 -= udiv(c2, dH) * H;
-          v[q][0] = llsrc[(size_t)c1 * llstride + c2];
-          v[q][1] = plane[(size_t)(H + c1) * G.n + c2];
-          v[q][2] = plane[(size_t)c1 * G.n + H + c2];
-          v[q][3] = plane[(size_t)(H + c1) * G.n + H + c2];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = k0 + threadIdx.x + q * blockDim.x;
-        if (e < CW * CW) {
-          LLs[e] = v[q][0];
-          HLs[e] = v[q][1];
-          LHs[e] = v[q][2];
-          HHs[e] = v[q][3];
-        }
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < CW * CW) {
+        LLs[e] = v[q][0];
+        HLs[e] = v[q][1];
+        LHs[e] = v[q][2];
+        HHs[e] = v[q][3];
       }
     }
     __syncthreads();
+    if (k + 1 < kend) issue(k + 1);
     // column synthesis: output row kappa1 in [0, 2TO), window column t2
     for (int t2 = threadIdx.x >> 5; t2 < CW; t2 += nw)
     for (int k1 = lane; k1 < 2 * TO; k1 += 32) {
@@ -432,7 +454,7 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
   basis_layout(c, dirac_plane, plane0, bl, nb);
   const int64_t N = (int64_t)c->n * c->n;
   const float scale = 1.0f / sqrtf((float)c->q);
-  if (dirac_plane >= 0) {
+  if (dirac_plane >= 0 && nb == 0) {
     int blocks = (int)std::min<int64_t>((N + 255) / 256, 1024);
     if (mode == kSaraPlain)
       PURIFY_LAUNCH(c, "dirac", s,
@@ -441,8 +463,6 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
     else
       PURIFY_LAUNCH(c, "dirac", s,
                     (k_dirac<kSaraProx><<<blocks, 256, 0, s>>>(x, nullptr, N, scale, pa, c->d_partials, c->d_sc)));
-  } else if (mode == kSaraProx) {
-    cudaMemsetAsync(&c->d_sc->f1, 0, sizeof(double), s);
   }
   if (nb == 0) {
     if (mode == kSaraProx) PURIFY_LAUNCH(c, "finish_zeta", s, (k_finish_zeta<<<1, 1, 0, s>>>(c->d_sc)));
@@ -454,10 +474,10 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
     const int L = c->n >> lev;
     const int H = L / 2;
     const int TI = tile_for(H);
-    LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale};
+    LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale, lev == 0, lev == 0 ? dirac_plane : -1};
     const float2* in = (lev == 0) ? x : c->d_ll[(lev - 1) & 1];
     float2* llo = c->d_ll[lev & 1];
-    dim3 grid(H / TI, H / TI, nb);
+    dim3 grid(H / TI, H / TI, nb + (G.dirac >= 0 ? 1 : 0));
     const size_t sm = dwt_smem(TI, 2 * maxp);
     if (mode == kSaraPlain)
       PURIFY_LAUNCH(c, "dwt_level", s,
@@ -488,7 +508,7 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
     const int L = c->n >> lev;  // output side
     const int H = L / 2;
     const int TO = tile_for(H);
-    LevelGeom G{TO, c->n, L, nb, plane0, lev == 0, scale};
+    LevelGeom G{TO, c->n, L, nb, plane0, lev == 0, scale, 0, -1};
     const bool from_plane = (lev == c->levels - 1);
     const float2* llin = from_plane ? nullptr : c->d_ll[(lev + 1) & 1];
     float2* llo = c->d_ll[lev & 1];
