@@ -485,6 +485,22 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   ia.s = st->sv;
   ia.w = st->qp;
   TRY(phi_forward_grid(c, k > 0 ? kRowInCgFinish : kRowInPlain, ia, s, k - 1));
+  // steps 7-9: the branches are independent until the next residual (§4.5:
+  // the proximity operators can run in parallel).  i = 1 (the prior) on the
+  // side stream, i = 2 (the data) on s; i = 3 is fused into the final pass.
+  TRY_CUDA(cudaEventRecord(st->ev_fork, s));
+  TRY_CUDA(cudaStreamWaitEvent(st->side, st->ev_fork, 0));
+  if (st->prior == PURIFY_PRIOR_TV) {
+    // TV prior (L1 = I): r1 = prox of gamma ||W grad .||_1 at x_hat + z1, z1, x1 = r1 - z1
+    TRY(tv_sdmm_branch(c, st, st->side));
+  } else {
+    // Psi^H x_hat with the soft threshold and dual update fused (u1 = r1 - z1), then x1 = Psi u1
+    SaraProxArgs pa{st->z1, st->u1, st->w};
+    TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, st->side));
+    TRY(sara_synthesis(c, st->u1, st->x1, st->side));
+  }
+  TRY_CUDA(cudaEventRecord(st->ev_join, st->side));
+  // i = 2: s2 = Phi x_hat and the l2 norms (FP64), the ball projection, z2 and v = u2 - s2
   DegridArgs da{};
   da.out = st->s2;
   da.z2 = st->z2;
@@ -492,29 +508,16 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   da.yb = st->yb;
   da.yscale = st->yscale;
   TRY(degrid(c, kDegridSdmm, da, s));
-  // distributed form (§4.5 eq. dbp1): one ball per block of visibilities
-  if (st->nblocks > 0) TRY(launch_block_norms(st, s));
-  if (st->prior == PURIFY_PRIOR_TV) {
-    // i = 1, TV prior (L1 = I): r1 = prox of gamma ||W grad .||_1 at x_hat + z1, z1, x1 = r1 - z1
-    TRY(tv_sdmm_branch(c, st, s));
-    TRY(launch_sdmm_l2_update(st, s));
-  } else {
-    // i = 1: Psi^H x_hat with the soft threshold and dual update fused; u1 = r1 - z1
-    SaraProxArgs pa{st->z1, st->u1, st->w};
-    TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, s));
-    // i = 2, second half: ball projection, z2 update, v = u2 - s2
-    TRY(launch_sdmm_l2_update(st, s));
-    // x1 = Psi u1
-    TRY(sara_synthesis(c, st->u1, st->x1, s));
-  }
-  // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual
+  if (st->nblocks > 0) TRY(launch_block_norms(st, s));  // distributed form: one ball per block
+  TRY(launch_sdmm_l2_update(st, s));
+  // x2 - Phi^H Phi x_hat = Phi^H v; i = 3 (positivity) and the next CG residual, after x1
   TRY(grid_adjoint(c, kGridSorted, st->v, s));
   RowOutArgs ra{};
   ra.out = st->r;
   ra.p = st->xhat;
   ra.x1 = st->x1;
   ra.z3 = st->z3;
-  TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s));
+  TRY(phi_adjoint_image(c, kRowOutSdmm, ra, s, nullptr, st->ev_join));
   st->launches_per_step = (int)(g_launches.load(std::memory_order_relaxed) - l0);
   return PURIFY_OK;
 }
@@ -792,6 +795,9 @@ void purify_sdmm_state_destroy(purify_sdmm_state* st) {
   cudaDeviceSynchronize();
   drop_graph(st);
   if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
+  if (st->side) cudaStreamDestroy(st->side);
+  if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+  if (st->ev_join) cudaEventDestroy(st->ev_join);
   void* ptrs[] = {st->xhat, st->r, st->p, st->qp, st->sv, st->x1, st->z3, st->z1, st->u1,
                   st->w, st->y, st->yb, st->yscale, st->z2, st->s2, st->v,
                   st->d_block_of, st->d_pos, st->d_bchunks, st->d_beps, st->d_bscale};
@@ -817,6 +823,12 @@ int purify_sdmm_state_create(purify_ctx* c, purify_sdmm_state** out) {
       (e = dev_alloc(&st->z2, M)) || (e = dev_alloc(&st->s2, M)) || (e = dev_alloc(&st->v, M))) {
     purify_sdmm_state_destroy(st);
     return e;
+  }
+  if (cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    purify_sdmm_state_destroy(st);
+    return PURIFY_E_CUDA;
   }
   purify_sdmm_default_params(&st->params);
   *out = st;

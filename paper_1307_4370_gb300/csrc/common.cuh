@@ -348,6 +348,8 @@ struct purify_sdmm_state {
   purify_sdmm_params params;
   // CUDA graph of one SDMM step (captured on a private stream, replayed on the caller's)
   cudaStream_t cap_stream;
+  cudaStream_t side;        // the SDMM prior branch (i = 1), concurrent with the data branch
+  cudaEvent_t ev_fork, ev_join;
   cudaGraphExec_t step_exec;
   // distributed form (§4.5 eq. dbp1): R balls over consecutive caller-order
   // blocks of the visibilities; nblocks = 0 is the single ball of eq. delta
@@ -416,7 +418,7 @@ int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s);
 int grid_adjoint(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s);
 int gram_grid(purify_ctx* c, cudaStream_t s);
 int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s,
-                      const float2* grid = nullptr);
+                      const float2* grid = nullptr, cudaEvent_t before_rows = nullptr);
 
 // sara.cu
 enum SaraMode { kSaraPlain = 0, kSaraProx = 1 };

@@ -420,7 +420,8 @@ int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStre
 }
 
 
-int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* grid) {
+int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* grid,
+                      cudaEvent_t before_rows) {
   const float* beam = c->beam_on ? c->d_beam : nullptr;
   const float2* Xg = grid ? grid : c->d_grid;
   const FftShape rs = row_shape(c), cs = col_shape(c);
@@ -435,6 +436,11 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
     allow_smem(k_col_inv<12>, smc);
     PURIFY_LAUNCH(c, "col_inv", s,
                   (k_col_inv<12><<<gc, cs.threads, smc, s>>>(Xg, c->d_half, c->d_tw, c->plan, c->n, cs.nsig)));
+  }
+  // the row pass may read operands of another stream (the SDMM prior branch)
+  if (before_rows) {
+    const int rc = check_cuda(cudaStreamWaitEvent(s, before_rows, 0));
+    if (rc != PURIFY_OK) return rc;
   }
 #define ROWI(E, MD)                                                                                          \
   do {                                                                                                       \
