@@ -228,6 +228,11 @@ __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
   return grid_slot_bytes(T, J) + (size_t)((T + J - 1) * (T + J - 1) + 1) * 4 + (size_t)((T / 2) * (T / 2) + 1) * 4;
 }
 constexpr size_t kGridSmemBudget = 72 * 1024;
+// 16-bit per-chunk tables of the gather: NK + 1 start-cell offsets, NO + 1
+// owner-work prefix values (stride rounded to 8 entries = 16 bytes)
+__host__ __device__ constexpr int grid_tab_stride(int T, int J) {
+  return (((T + J - 1) * (T + J - 1) + 1 + (T / 2) * (T / 2) + 1) + 7) / 8 * 8;
+}
 }  // namespace purify
 
 struct purify_ctx {
@@ -264,6 +269,8 @@ struct purify_ctx {
   int nchunks;
   int chunk_max;
   int4* d_chunks;       // (tile, begin, end, slot or -1)
+  uint16_t* d_chunk_tab; // per chunk: start-cell offsets and owner-work prefix (grid_tab_stride entries)
+  int chunk_tab_stride;
   int* d_tile_slot0;    // first slot of a multi-chunk tile
   int* d_tile_nchunk;   // chunks per tile
   unsigned* d_tile_cnt; // arrival counters (zero between launches)

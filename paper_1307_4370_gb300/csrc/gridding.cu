@@ -160,34 +160,6 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // chunk order.  Every cell is written once and the result does not depend
 // on scheduling.
 // ---------------------------------------------------------------------------
-// Exclusive prefix sum of one int per thread over the block (blockDim a
-// multiple of 32); *total gets the block sum.
-__device__ __forceinline__ int block_excl_scan(int v, int* wsum, int* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int x = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += t;
-    }
-    if (lane < nw) wsum[lane] = x;  // inclusive warp totals
-  }
-  __syncthreads();
-  const int excl = incl - v + (wid > 0 ? wsum[wid - 1] : 0);
-  *total = wsum[nw - 1];
-  __syncthreads();
-  return excl;
-}
-
 struct Acc4 {  // a 2 x 2 block of complex sums
   float2 a00, a01, a10, a11;
 };
@@ -197,6 +169,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
                                                        const int* __restrict__ perm, const float2* __restrict__ vis,
                                                        const int4* __restrict__ list,
                                                        const int4* __restrict__ chunks,
+                                                       const uint16_t* __restrict__ tab, int tab_stride,
                                                        const int* __restrict__ tile_slot0,
                                                        const int* __restrict__ tile_nchunk,
                                                        unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
@@ -206,7 +179,6 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
   extern __shared__ float4 sm4[];
   __shared__ bool s_last;
-  __shared__ int wsum[NT / 32];
   const int W = T + J - 1, NK = W * W, HB = T / 2, NO = HB * HB;
   const int lhb = __ffs(HB) - 1;  // T is a power of two
   float4* part = sm4;  // slot j: first[j] at 4j, last[j] at 4j + 2 (Gram form: the halo first)
@@ -225,7 +197,19 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   // degridded sample, in the same order of operations as k_degrid
   const int HW = T + 2 * (J - 1);
   float2* halo = reinterpret_cast<float2*>(sm4);
-  // the first four list entries of each thread, in flight with the halo loads
+  // this chunk's start-cell offsets and owner-work prefix (16-bit, set up
+  // with the lists), the first four list entries of each thread, and the
+  // halo: all in flight together
+  // 16-byte groups per thread: grid_tab_stride / 8 / 256 <= 3 for T <= 64, and
+  // 1 for the chunks small enough for five CTAs per SM (T <= 32)
+  constexpr int kTabMax = MINB >= 5 ? 1 : 3;
+  uint4 tv[kTabMax];
+  const uint4* tab4 = reinterpret_cast<const uint4*>(tab + (size_t)blockIdx.x * tab_stride);
+#pragma unroll
+  for (int q = 0; q < kTabMax; ++q) {
+    const int i = threadIdx.x + q * NT;
+    if (i < tab_stride / 8) tv[q] = __ldg(&tab4[i]);
+  }
   int4 le[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -311,69 +295,23 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
     }
   }
   __syncthreads();
-  // ---- off[k] = first entry with key >= k (keys are sorted): first the
-  // start of every start row (in the owner-prefix space, free until below),
-  // then each key by a binary search inside its row; each thread takes a
-  // contiguous run of keys
-  {
-    int* rowoff = P;  // W + 1 <= (T / 2)^2 + 1 entries
-    for (int kr = threadIdx.x; kr <= W; kr += NT) {
-      const int k = kr * W;
-      int lo = 0, hi = ne;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (key[mid] < k) lo = mid + 1;
-        else hi = mid;
+  // ---- the tables into shared memory
+#pragma unroll
+  for (int q = 0; q < kTabMax; ++q) {
+    const int i = threadIdx.x + q * NT;
+    if (i < tab_stride / 8) {
+      const uint32_t w[4] = {tv[q].x, tv[q].y, tv[q].z, tv[q].w};
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int idx = 8 * i + h;
+        const int v = (int)((w[h >> 1] >> (16 * (h & 1))) & 0xffffu);
+        if (idx <= NK) off[idx] = v;
+        else if (idx - (NK + 1) <= NO) P[idx - (NK + 1)] = v;
       }
-      rowoff[kr] = lo;
-    }
-    __syncthreads();
-    const int per = (NK + 1 + NT - 1) / NT;
-    const int k0 = threadIdx.x * per, k1 = min(k0 + per, NK + 1);
-    int lo = 0;
-    for (int k = k0; k < k1; ++k) {
-      const int kr = k / W;
-      lo = max(lo, rowoff[kr]);
-      int hi = rowoff[min(kr + 1, W)];
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (key[mid] < k) lo = mid + 1;
-        else hi = mid;
-      }
-      off[k] = lo;
     }
   }
   __syncthreads();
-  // ---- work of each owner (entries over its J + 1 runs), prefix over owners
-  int Wt;
-  {
-    constexpr int kMaxPer = 4;  // owners per thread: (T / 2)^2 / 256 <= 4 for T <= 64
-    const int per = (NO + NT - 1) / NT;
-    const int o0 = threadIdx.x * per;
-    int cnt[kMaxPer];
-    int run = 0;
-#pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) {
-      const int o = o0 + q;
-      cnt[q] = 0;
-      if (q < per && o < NO) {
-        const int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
-        for (int kr = R; kr <= R + J; ++kr) cnt[q] += off[kr * W + C + J + 1] - off[kr * W + C];
-      }
-      run += cnt[q];
-    }
-    int base = block_excl_scan(run, wsum, &Wt);
-#pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) {
-      const int o = o0 + q;
-      if (q < per && o < NO) {
-        P[o] = base;
-        base += cnt[q];
-      }
-    }
-    if (threadIdx.x == 0) P[NO] = Wt;
-  }
-  __syncthreads();
+  const int Wt = P[NO];
   const bool multi = ch.w >= 0;
   float2* dst = multi ? slots + (size_t)ch.w * T * T : nullptr;
   auto write_owner = [&](int o, const Acc4& a) {
@@ -551,7 +489,8 @@ static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cu
     allow_smem(k_grid<J, MD, MINB>, sm);                                                                       \
     PURIFY_LAUNCH(c, NAME, s,                                                                                  \
                   (k_grid<J, MD, MINB><<<c->nchunks, kGridThreads, sm, s>>>(                                   \
-                      OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_tile_slot0, c->d_tile_nchunk,      \
+                      OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_chunk_tab, c->chunk_tab_stride,     \
+                      c->d_tile_slot0, c->d_tile_nchunk,                                                        \
                       c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max)));   \
   } while (0)
   if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
