@@ -68,3 +68,39 @@ def test_batch_rejects_shared_context():
     a, b = ctx.sdmm_state(), ctx.sdmm_state()
     with pytest.raises(binding.PurifyError):
         binding.Batch([a, b])
+
+
+def test_batch_with_mixed_forms():
+    """One batch of problems that use the options of the state: the TV prior,
+    the distributed data blocks, the Gaussian kernel with a primary beam; each
+    follows the iterates it has alone."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    iters = 5
+    probs = [make(s) for s in SPECS[:3]]
+
+    def build(k, w, p, y, eps):
+        kernel = "gauss" if k == 2 else "kb"
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J, kernel=kernel)
+        if k == 2:
+            ctx.set_beam(np.linspace(0.5, 1.0, w.n * w.n).reshape(w.n, w.n))
+        st = ctx.sdmm_state()
+        if k == 0:
+            st.set_prior("tv", fgp_iters=10)
+        st.init(dev(y, torch), eps)
+        if k == 1:
+            st.set_blocks([0, w.M // 3, w.M], [eps * 0.6, eps * 0.8])
+        return ctx, st
+
+    made = [build(k, *pr) for k, pr in enumerate(probs)]
+    batch = binding.Batch([st for _, st in made])
+    batch.step(iters)
+    torch.cuda.synchronize()
+    xb = [host(st.get_image()) for _, st in made]
+    for k, pr in enumerate(probs):
+        _, st = build(k, *pr)
+        for _ in range(iters):
+            st.step()
+        assert rel_err(xb[k], host(st.get_image())) <= 1e-6
+    batch.close()
