@@ -263,7 +263,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -385,36 +385,66 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   std::stable_sort(chunks.begin(), chunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
   c->nchunks = (int)chunks.size();
   c->nslots = nslots;
-  // per chunk, the gather's tables (they depend on the frequencies only):
-  // off[k] = first entry with start-cell key >= k (k = 0..NK) and the prefix
-  // P[o] of the owners' work (2 x 2 cell blocks, o = 0..NO), as 16-bit values
-  const int NK = W * W, HB = T / 2, NO = HB * HB;
+  // per chunk, the gather's walk (it depends on the frequencies only): the
+  // prefix P[o] of the owners' work (2 x 2 cell blocks, o = 0..NO) as 16-bit
+  // values, and the items of the steps of each thread's slice, step-major
+  const int NK = W * W, HB = T / 2, NO = HB * HB, NT = purify::kGridThreads;
   c->chunk_tab_stride = purify::grid_tab_stride(T, J);
   std::vector<uint16_t> tab((size_t)c->nchunks * c->chunk_tab_stride, 0);
-  bool tab_overflow = false;
+  std::vector<int> item_row(c->nchunks);
+  std::vector<uint32_t> items;
+  bool tab_overflow = c->chunk_max > (1 << purify::kItemEntryBits) || NO > 1024 || J > 8;
   {
     std::vector<int> off(NK + 1);
-    for (int q = 0; q < c->nchunks; ++q) {
+    int64_t rows = 0;
+    for (int q = 0; q < c->nchunks && !tab_overflow; ++q) {
       const int4 ch = chunks[q];
       const int* kb = lkey.data() + ch.y;
       const int ne = ch.z - ch.y;
+      // off[k] = first entry with start-cell key >= k (k = 0..NK)
       for (int k = 0, e = 0; k <= NK; ++k) {
         while (e < ne && kb[e] < k) ++e;
         off[k] = e;
       }
       uint16_t* t = tab.data() + (size_t)q * c->chunk_tab_stride;
-      for (int k = 0; k <= NK; ++k) t[k] = (uint16_t)off[k];
       int acc = 0;
       for (int o = 0; o < NO; ++o) {
-        t[NK + 1 + o] = (uint16_t)acc;
+        t[o] = (uint16_t)acc;
         const int R = 2 * (o / HB), C = 2 * (o % HB);
         for (int kr = R; kr <= R + J; ++kr) acc += off[kr * W + C + J + 1] - off[kr * W + C];
       }
-      t[NK + 1 + NO] = (uint16_t)acc;
-      if (acc > 65535) tab_overflow = true;  // not reachable with chunk_max <= 864 (<= 25 owners per entry)
+      t[NO] = (uint16_t)acc;
+      if (acc > 65535) {  // not reachable with chunk_max <= 864 (<= 25 owners per entry)
+        tab_overflow = true;
+        break;
+      }
+      // thread j walks steps [t0(j), t0(j + 1)) of the owners' concatenated runs
+      const int Wt = acc;
+      const int64_t nrow = (Wt + NT - 1) / NT;
+      item_row[q] = (int)rows;
+      items.resize((size_t)(rows + nrow) * NT, 0u);
+      uint32_t* dst = items.data() + (size_t)rows * NT;
+      rows += nrow;
+      auto t0_of = [&](int jj) { return (int)(((int64_t)jj * Wt + NT - 1) / NT); };
+      int jj = 0, tj0 = 0, tj1 = t0_of(1), tt = 0;
+      for (int o = 0; o < NO; ++o) {
+        const int R = 2 * (o / HB), C = 2 * (o % HB);
+        for (int kr = R; kr <= R + J; ++kr) {
+          for (int e = off[kr * W + C]; e < off[kr * W + C + J + 1]; ++e, ++tt) {
+            while (tt >= tj1) {
+              ++jj;
+              tj0 = tj1;
+              tj1 = t0_of(jj + 1);
+            }
+            const int kc = kb[e] - kr * W;  // start column, in [C, C + J]
+            dst[(size_t)(tt - tj0) * NT + jj] = purify::grid_item(e, R + J - kr, C + J - kc, o);
+          }
+        }
+      }
     }
+    c->nitem_rows = rows;
   }
-  if (tab_overflow) {
+  if (tab_overflow || c->nitem_rows > INT32_MAX) {
     cudaFree(d_uv_user);
     cudaFree(d_k0);
     return PURIFY_E_SIZE;
@@ -439,6 +469,8 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       (st = dev_alloc(&c->d_list, c->nlist)) == PURIFY_OK && (st = dev_alloc(&d_lk, c->nlist)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_chunks, c->nchunks)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_chunk_tab, (size_t)c->nchunks * c->chunk_tab_stride)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_items, (size_t)std::max<int64_t>(1, c->nitem_rows) * NT)) == PURIFY_OK &&
+      (st = dev_alloc(&c->d_item_row, c->nchunks)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_dchunks, std::max(1, c->ndchunks))) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_slot0, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_nchunk, c->ntiles)) == PURIFY_OK &&
@@ -456,6 +488,8 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
     }
     cudaMemcpyAsync(c->d_chunks, chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_chunk_tab, tab.data(), tab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s);
+    if (!items.empty()) cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_item_row, item_row.data(), c->nchunks * sizeof(int), cudaMemcpyHostToDevice, s);
     if (c->ndchunks > 0)
       cudaMemcpyAsync(c->d_dchunks, dchunks.data(), c->ndchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_tile_slot0, slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);

@@ -207,14 +207,14 @@ extern std::atomic<unsigned long long> g_launches;
 // ---------------------------------------------------------------------------
 // The context (opaque to callers).
 // ---------------------------------------------------------------------------
-// Shared-memory layout of one gridding chunk (k_grid): per entry a start-cell
-// key, the value and the zero-padded row and column kernel weights (stride
-// kept odd against bank conflicts); per CTA the start-cell run offsets, the
-// prefix of the cell blocks' work and two partial-sum slots per thread.
+// Shared-memory layout of one gridding chunk (k_grid): per entry the value
+// and the zero-padded row and column kernel weights (stride kept odd against
+// bank conflicts); per CTA the prefix of the cell blocks' work and two
+// partial-sum slots per thread.
 namespace purify {
 constexpr int kGridThreads = 256;
 __host__ __device__ constexpr int grid_wstride(int J) { return 2 * (J + 2) + 1; }
-__host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 4 + 8 + 4 * (size_t)grid_wstride(J); }
+__host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 8 + 4 * (size_t)grid_wstride(J); }
 // The partial-sum slots share their space with the grid halo that the Gram
 // form (G^T G in one pass) stages before the entries.
 __host__ __device__ constexpr size_t grid_halo_bytes(int T, int J) {
@@ -225,13 +225,18 @@ __host__ __device__ constexpr size_t grid_slot_bytes(int T, int J) {
                                                                 : (size_t)2 * kGridThreads * 32;
 }
 __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
-  return grid_slot_bytes(T, J) + (size_t)((T + J - 1) * (T + J - 1) + 1) * 4 + (size_t)((T / 2) * (T / 2) + 1) * 4;
+  return grid_slot_bytes(T, J) + (size_t)((T / 2) * (T / 2) + 1) * 4;
 }
 constexpr size_t kGridSmemBudget = 72 * 1024;
-// 16-bit per-chunk tables of the gather: NK + 1 start-cell offsets, NO + 1
-// owner-work prefix values (stride rounded to 8 entries = 16 bytes)
-__host__ __device__ constexpr int grid_tab_stride(int T, int J) {
-  return (((T + J - 1) * (T + J - 1) + 1 + (T / 2) * (T / 2) + 1) + 7) / 8 * 8;
+// 16-bit per-chunk table of the gather: the NO + 1 owner-work prefix values
+// (stride rounded to 8 entries = 16 bytes)
+__host__ __device__ constexpr int grid_tab_stride(int T, int J) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }
+// One gather step of the gridding: a 32-bit item (entry index in the chunk,
+// padded row tap of the block's first cell row, padded column tap of its
+// first cell column, cell block), 12 + 4 + 4 + 10 bits.
+constexpr int kItemEntryBits = 12;
+__host__ __device__ constexpr uint32_t grid_item(int e, int ar, int bc, int o) {
+  return (uint32_t)e | ((uint32_t)ar << 12) | ((uint32_t)bc << 16) | ((uint32_t)o << 20);
 }
 }  // namespace purify
 
@@ -269,8 +274,12 @@ struct purify_ctx {
   int nchunks;
   int chunk_max;
   int4* d_chunks;       // (tile, begin, end, slot or -1)
-  uint16_t* d_chunk_tab; // per chunk: start-cell offsets and owner-work prefix (grid_tab_stride entries)
+  uint16_t* d_chunk_tab; // per chunk: owner-work prefix (grid_tab_stride entries)
   int chunk_tab_stride;
+  uint32_t* d_items;    // per chunk, the gather steps of its threads (grid_item), step-major:
+                        // step s of thread j at d_items[(item_row[chunk] + s) * kGridThreads + j]
+  int* d_item_row;      // per chunk, its first row of d_items
+  int64_t nitem_rows;
   int* d_tile_slot0;    // first slot of a multi-chunk tile
   int* d_tile_nchunk;   // chunks per tile
   unsigned* d_tile_cnt; // arrival counters (zero between launches)

@@ -147,14 +147,17 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // set-up listed, per tile, the visibilities whose footprint meets it, sorted
 // by the footprint's first cell relative to the tile (one run per start
 // cell), and cut each list into chunks.  One CTA per chunk stages its
-// entries (start cell, value, J + J kernel weights) in shared memory.  A
-// 2 x 2 block of cells ("owner") sums, in a fixed order, the entries of the
-// (J + 1)^2 start cells whose footprint reaches it: J + 1 runs of the sorted
-// list, one per start row.  The owners' work is uneven (dense start cells
-// where tracks cross), so the CTA splits the concatenation of all owners'
-// runs into equal slices, one per thread (merge-path style): a thread writes
-// the owners that lie inside its slice and leaves two partial sums for the
-// owners cut by its slice ends, which are added afterwards in slice order.
+// entries (value, J + J kernel weights) in shared memory.  A 2 x 2 block of
+// cells ("owner") sums, in a fixed order, the entries of the (J + 1)^2 start
+// cells whose footprint reaches it: J + 1 runs of the sorted list, one per
+// start row.  The owners' work is uneven (dense start cells where tracks
+// cross), so the concatenation of all owners' runs is split into equal
+// slices, one per thread (merge-path style): a thread writes the owners that
+// lie inside its slice and leaves two partial sums for the owners cut by its
+// slice ends, which are added afterwards in slice order.  The walk depends
+// on the frequencies only, so set-up stores it: one 32-bit item per step
+// (entry, owner, row and column tap), laid out step-major so that the loads
+// of one step by a warp are contiguous.
 // A tile with one chunk is written to X directly; otherwise each chunk
 // stores a partial tile and the last chunk to finish adds the partials in
 // chunk order.  Every cell is written once and the result does not depend
@@ -170,6 +173,8 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
                                                        const int4* __restrict__ list,
                                                        const int4* __restrict__ chunks,
                                                        const uint16_t* __restrict__ tab, int tab_stride,
+                                                       const uint32_t* __restrict__ items,
+                                                       const int* __restrict__ item_row,
                                                        const int* __restrict__ tile_slot0,
                                                        const int* __restrict__ tile_nchunk,
                                                        unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
@@ -179,14 +184,12 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
   extern __shared__ float4 sm4[];
   __shared__ bool s_last;
-  const int W = T + J - 1, NK = W * W, HB = T / 2, NO = HB * HB;
+  const int W = T + J - 1, HB = T / 2, NO = HB * HB;
   const int lhb = __ffs(HB) - 1;  // T is a power of two
   float4* part = sm4;  // slot j: first[j] at 4j, last[j] at 4j + 2 (Gram form: the halo first)
   float2* yv = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm4) + grid_slot_bytes(T, J));
   float* wt = reinterpret_cast<float*>(yv + chunk_max);
-  int* key = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);
-  int* off = key + chunk_max;  // NK + 1 run offsets
-  int* P = off + NK + 1;       // NO + 1 work prefix of the owners
+  int* P = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);  // NO + 1 work prefix of the owners
   const int4 ch = chunks[blockIdx.x];
   const int tile = ch.x;
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
@@ -197,19 +200,12 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   // degridded sample, in the same order of operations as k_degrid
   const int HW = T + 2 * (J - 1);
   float2* halo = reinterpret_cast<float2*>(sm4);
-  // this chunk's start-cell offsets and owner-work prefix (16-bit, set up
-  // with the lists), the first four list entries of each thread, and the
-  // halo: all in flight together
-  // 16-byte groups per thread: grid_tab_stride / 8 / 256 <= 3 for T <= 64, and
-  // 1 for the chunks small enough for five CTAs per SM (T <= 32)
-  constexpr int kTabMax = MINB >= 5 ? 1 : 3;
-  uint4 tv[kTabMax];
+  // this chunk's owner-work prefix (16-bit, set up with the lists; one
+  // 16-byte group per thread for T <= 64), the first four list entries of
+  // each thread, and the halo: all in flight together
+  uint4 tv;
   const uint4* tab4 = reinterpret_cast<const uint4*>(tab + (size_t)blockIdx.x * tab_stride);
-#pragma unroll
-  for (int q = 0; q < kTabMax; ++q) {
-    const int i = threadIdx.x + q * NT;
-    if (i < tab_stride / 8) tv[q] = __ldg(&tab4[i]);
-  }
+  if (threadIdx.x < tab_stride / 8) tv = __ldg(&tab4[threadIdx.x]);
   int4 le[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -280,7 +276,6 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
         }
         val[q] = acc;
       }
-      key[e] = le[q].y;
       yv[e] = val[q];
       float* w = wt + (size_t)e * S;
       w[0] = 0.f;
@@ -295,19 +290,13 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
     }
   }
   __syncthreads();
-  // ---- the tables into shared memory
+  // ---- the owner-work prefix into shared memory
+  if (threadIdx.x < tab_stride / 8) {
+    const uint32_t w[4] = {tv.x, tv.y, tv.z, tv.w};
 #pragma unroll
-  for (int q = 0; q < kTabMax; ++q) {
-    const int i = threadIdx.x + q * NT;
-    if (i < tab_stride / 8) {
-      const uint32_t w[4] = {tv[q].x, tv[q].y, tv[q].z, tv[q].w};
-#pragma unroll
-      for (int h = 0; h < 8; ++h) {
-        const int idx = 8 * i + h;
-        const int v = (int)((w[h >> 1] >> (16 * (h & 1))) & 0xffffu);
-        if (idx <= NK) off[idx] = v;
-        else if (idx - (NK + 1) <= NO) P[idx - (NK + 1)] = v;
-      }
+    for (int h = 0; h < 8; ++h) {
+      const int idx = 8 * threadIdx.x + h;
+      if (idx <= NO) P[idx] = (int)((w[h >> 1] >> (16 * (h & 1))) & 0xffffu);
     }
   }
   __syncthreads();
@@ -325,37 +314,22 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       reinterpret_cast<float4*>(dst + (R + 1) * T + C)[0] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
     }
   };
-  // ---- this thread's slice [t0, t1) of the concatenated runs, walked as one
-  // flat loop (one entry per step) so the lanes of a warp stay in step
+  // ---- this thread's slice [t0, t1) of the concatenated runs, one stored
+  // item per step (the lanes of a warp stay in step)
   const int j = threadIdx.x;
   const int t0 = (j * Wt + NT - 1) / NT, t1 = ((j + 1) * Wt + NT - 1) / NT;
   const int nmy = t1 - t0;
   if (nmy > 0) {
-    int o = 0;  // owner holding t0: the last o with P[o] <= t0
-    {
-      int hi = NO - 1;
-      while (o < hi) {
-        const int mid = (o + hi + 1) >> 1;
-        if (P[mid] <= t0) o = mid;
-        else hi = mid - 1;
-      }
-    }
-    int Po = P[o], Pe = P[o + 1];
-    int R = 2 * (o >> lhb), C = 2 * (o & (HB - 1));
-    int kr = R, ee = 0, run_end = 0;
-    for (int local = t0 - Po;; ++kr) {  // the run of o holding t0
-      const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
-      if (local < s1 - s0) {
-        ee = s0 + local;
-        run_end = s1;
-        break;
-      }
-      local -= s1 - s0;
-    }
-    int a0 = R + J - 1 - kr, kbase = kr * W;  // row taps of cell rows R, R + 1: padded index a0 + 1, a0 + 2
+    const uint32_t* its = items + (size_t)item_row[blockIdx.x] * NT + j;
+    constexpr int PF = MINB >= 5 ? 4 : 8;  // items in flight per thread
+    uint32_t pf[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) pf[q] = q < nmy ? __ldcs(&its[(size_t)q * NT]) : 0u;
+    int o = (int)(pf[0] >> 20);
     Acc4 a;
     a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
     auto flush = [&]() {
+      const int Po = P[o], Pe = P[o + 1];
       if (Po >= t0 && Pe <= t1) {
         write_owner(o, a);
       } else {
@@ -364,41 +338,31 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
         sl[1] = make_float4(a.a10.x, a.a10.y, a.a11.x, a.a11.y);
       }
     };
-    for (int step = 0; step < nmy; ++step) {
-      const int b0 = C + J - 1 - (key[ee] - kbase);  // column tap of cell column C, in [-1, J - 1]
-      const float2 v = yv[ee];
-      const float* w = wt + ee * S;
-      const float wr0 = w[a0 + 1], wr1 = w[a0 + 2];
-      const float wc0 = w[J + 3 + b0], wc1 = w[J + 4 + b0];
-      const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
-      a.a00.x = fmaf(wc0, v0.x, a.a00.x); a.a00.y = fmaf(wc0, v0.y, a.a00.y);
-      a.a01.x = fmaf(wc1, v0.x, a.a01.x); a.a01.y = fmaf(wc1, v0.y, a.a01.y);
-      a.a10.x = fmaf(wc0, v1.x, a.a10.x); a.a10.y = fmaf(wc0, v1.y, a.a10.y);
-      a.a11.x = fmaf(wc1, v1.x, a.a11.x); a.a11.y = fmaf(wc1, v1.y, a.a11.y);
-      if (++ee == run_end && step + 1 < nmy) {
-        // next non-empty run of this owner, else the next owner with work
-        for (;;) {
-          if (++kr > R + J) {
+    for (int s0 = 0; s0 < nmy; s0 += PF) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const int st = s0 + q;
+        if (st < nmy) {
+          const uint32_t it = pf[q];
+          if (st + PF < nmy) pf[q] = __ldcs(&its[(size_t)(st + PF) * NT]);
+          const int oi = (int)(it >> 20);
+          if (oi != o) {
             flush();
             a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
-            do {
-              ++o;
-              Po = Pe;
-              Pe = P[o + 1];
-            } while (Pe == Po);
-            R = 2 * (o >> lhb);
-            C = 2 * (o & (HB - 1));
-            kr = R;
+            o = oi;
           }
-          const int s0 = off[kr * W + C], s1 = off[kr * W + C + J + 1];
-          if (s1 > s0) {
-            ee = s0;
-            run_end = s1;
-            break;
-          }
+          const int ee = (int)(it & ((1u << kItemEntryBits) - 1));
+          const int ar = (int)((it >> 12) & 15u), bc = (int)((it >> 16) & 15u);
+          const float2 v = yv[ee];
+          const float* w = wt + ee * S;
+          const float wr0 = w[ar], wr1 = w[ar + 1];
+          const float wc0 = w[J + 2 + bc], wc1 = w[J + 3 + bc];
+          const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
+          a.a00.x = fmaf(wc0, v0.x, a.a00.x); a.a00.y = fmaf(wc0, v0.y, a.a00.y);
+          a.a01.x = fmaf(wc1, v0.x, a.a01.x); a.a01.y = fmaf(wc1, v0.y, a.a01.y);
+          a.a10.x = fmaf(wc0, v1.x, a.a10.x); a.a10.y = fmaf(wc0, v1.y, a.a10.y);
+          a.a11.x = fmaf(wc1, v1.x, a.a11.x); a.a11.y = fmaf(wc1, v1.y, a.a11.y);
         }
-        a0 = R + J - 1 - kr;
-        kbase = kr * W;
       }
     }
     flush();
@@ -490,6 +454,7 @@ static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cu
     PURIFY_LAUNCH(c, NAME, s,                                                                                  \
                   (k_grid<J, MD, MINB><<<c->nchunks, kGridThreads, sm, s>>>(                                   \
                       OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_chunk_tab, c->chunk_tab_stride,     \
+                      c->d_items, c->d_item_row,                                                                \
                       c->d_tile_slot0, c->d_tile_nchunk,                                                        \
                       c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max)));   \
   } while (0)
