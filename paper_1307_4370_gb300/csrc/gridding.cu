@@ -163,6 +163,14 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // chunk order.  Every cell is written once and the result does not depend
 // on scheduling.
 // ---------------------------------------------------------------------------
+// floor(k / d) for 0 <= k < 2^16 and 1 <= d <= 128 from the rounded
+// reciprocal r = 1/d: (k + 1/2) r lies at least 1/(2d) from an integer and
+// its rounding error is below 2^-22 (k + 1/2)/d, so truncation is exact
+// (checked exhaustively over that range by a host test).
+__device__ __forceinline__ int quot_small(int k, float r) {
+  return __float2int_rz(__fmul_rn(__fadd_rn((float)k, 0.5f), r));
+}
+
 struct Acc4 {  // a 2 x 2 block of complex sums
   float2 a00, a01, a10, a11;
 };
@@ -199,6 +207,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   // footprints of the tile's entries cover; each entry's value is then its
   // degridded sample, in the same order of operations as k_degrid
   const int HW = T + 2 * (J - 1);
+  const float inv_hw = 1.0f / (float)HW, inv_w = 1.0f / (float)W;
   float2* halo = reinterpret_cast<float2*>(sm4);
   // this chunk's owner-work prefix (16-bit, set up with the lists; one
   // 16-byte group per thread for T <= 64), the first four list entries of
@@ -219,7 +228,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       for (int q = 0; q < 8; ++q) {
         const int k = k0 + threadIdx.x + q * NT;
         if (k < HW * HW) {
-          const int rr = k / HW, cc = k - rr * HW;
+          const int rr = quot_small(k, inv_hw), cc = k - rr * HW;
           int r = R0 - (J - 1) + rr, c = C0 - (J - 1) + cc;
           if (r < 0) r += L;
           if (r >= L) r -= L;
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       kb_weights<J>(kb, __int_as_float(le[q].z), wr);
       kb_weights<J>(kb, __int_as_float(le[q].w), wc);
       if constexpr (MODE == kGridGram) {
-        const int kr = le[q].y / W, kc = le[q].y - kr * W;  // footprint start in the halo
+        const int kr = quot_small(le[q].y, inv_w), kc = le[q].y - kr * W;  // footprint start in the halo
         const float2* base = halo + kr * HW + kc;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
