@@ -32,7 +32,8 @@ def nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    """CUDA translation units and the plain C++ host ones (the gather plan)."""
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def headers() -> list[str]:
@@ -60,7 +61,7 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags: list[
     procs = []
     objs = []
     for src in sources():
-        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         cmd = [cc, *flags, "-c", src, "-o", obj]
         if verbose:

@@ -293,178 +293,33 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
     cudaFree(d_k0);
     return PURIFY_E_CUDA;
   }
-  const int T = c->tileT, TD = c->tiles_1d, J = c->J, L = c->L;
-  // counting sort by home tile (stable: keeps the caller's order inside a tile)
-  std::vector<int> cnt(c->ntiles + 1, 0), perm(M);
-  for (int64_t i = 0; i < M; ++i) cnt[(k0[i].x / T) * TD + k0[i].y / T + 1]++;
-  for (int t = 0; t < c->ntiles; ++t) cnt[t + 1] += cnt[t];
-  {
-    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int64_t i = 0; i < M; ++i) perm[pos[(k0[i].x / T) * TD + k0[i].y / T]++] = (int)i;
-  }
-  // per-tile lists of sorted indices whose footprint meets the tile
-  std::vector<int> lcnt(c->ntiles + 1, 0);
-  auto tiles_of = [&](int64_t si, int* tl) {
-    const int2 k = k0[perm[si]];
-    const int r0 = k.x / T, r1 = ((k.x + J - 1) % L) / T;
-    const int c0 = k.y / T, c1 = ((k.y + J - 1) % L) / T;
-    int nt = 0;
-    const int rs[2] = {r0, r1}, cs[2] = {c0, c1};
-    for (int a = 0; a < (r1 != r0 ? 2 : 1); ++a)
-      for (int b = 0; b < (c1 != c0 ? 2 : 1); ++b) tl[nt++] = rs[a] * TD + cs[b];
-    return nt;
-  };
-  int tl[4];
-  for (int64_t si = 0; si < M; ++si) {
-    const int nt = tiles_of(si, tl);
-    for (int k = 0; k < nt; ++k) lcnt[tl[k] + 1]++;
-  }
-  for (int t = 0; t < c->ntiles; ++t) lcnt[t + 1] += lcnt[t];
-  c->nlist = lcnt[c->ntiles];
-  std::vector<int> list(c->nlist);
-  {
-    std::vector<int> pos(lcnt.begin(), lcnt.end() - 1);
-    for (int64_t si = 0; si < M; ++si) {
-      const int nt = tiles_of(si, tl);
-      for (int k = 0; k < nt; ++k) list[pos[tl[k]]++] = (int)si;
-    }
-  }
-  // order each tile's list by the footprint start cell relative to the tile
-  // (key = (dr + J - 1) * W + (dc + J - 1), W = T + J - 1): the gridding
-  // kernel finds the visibilities starting at a given cell as one run
-  const int W = T + J - 1;
-  auto rel = [&](int k, int origin) {  // start offset in [-(J-1), L - J + 1)
-    int t = (k - origin) % L;
-    if (t < 0) t += L;
-    return t >= L - (J - 1) ? t - L : t;
-  };
-  std::vector<int> lkey(c->nlist);
-  {
-    std::vector<std::pair<int, int>> seg;
-    for (int t = 0; t < c->ntiles; ++t) {
-      const int R0 = (t / TD) * T, C0 = (t % TD) * T;
-      seg.clear();
-      for (int e = lcnt[t]; e < lcnt[t + 1]; ++e) {
-        const int2 k = k0[perm[list[e]]];
-        const int key = (rel(k.x, R0) + J - 1) * W + (rel(k.y, C0) + J - 1);
-        seg.emplace_back(key, list[e]);
-      }
-      std::stable_sort(seg.begin(), seg.end(),
-                       [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
-      for (size_t k = 0; k < seg.size(); ++k) {
-        list[lcnt[t] + k] = seg[k].second;
-        lkey[lcnt[t] + k] = seg[k].first;
-      }
-    }
-  }
-  // gridding work units: each tile's list in chunks whose entries, with the
-  // kernel's fixed tables, fit a shared-memory budget that keeps three CTAs
-  // resident per SM
-  const int64_t mean = (c->nlist + c->ntiles - 1) / c->ntiles;
-  // (large tiles: room for at least 512 entries beyond the fixed tables, even
-  // if fewer CTAs then fit on an SM)
-  const int64_t fixed = (int64_t)purify::grid_fixed_bytes(T, J), per = (int64_t)purify::grid_entry_bytes(J);
-  const int64_t budget = std::max<int64_t>((int64_t)purify::kGridSmemBudget, fixed + 512 * per);
-  const int cap = (int)std::max<int64_t>(128, (budget - fixed) / per / 32 * 32);
-  c->chunk_max = (int)std::min<int64_t>(cap, std::max<int64_t>(256, ((3 * mean / 2 + 127) / 128) * 128));
-  std::vector<int4> chunks;
-  std::vector<int> slot0(c->ntiles, -1), nchunk(c->ntiles, 0);
-  int nslots = 0;
-  for (int t = 0; t < c->ntiles; ++t) {
-    const int b = lcnt[t], e = lcnt[t + 1];
-    const int nc = std::max(1, (e - b + c->chunk_max - 1) / c->chunk_max);
-    nchunk[t] = nc;
-    if (nc > 1) slot0[t] = nslots;
-    for (int k = 0; k < nc; ++k) {
-      const int cb = b + (int)((int64_t)(e - b) * k / nc), ce = b + (int)((int64_t)(e - b) * (k + 1) / nc);
-      chunks.push_back(make_int4(t, cb, ce, nc > 1 ? nslots + k : -1));
-    }
-    if (nc > 1) nslots += nc;
-  }
-  // heavy chunks first
-  std::stable_sort(chunks.begin(), chunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
-  c->nchunks = (int)chunks.size();
-  c->nslots = nslots;
-  // per chunk, the gather's walk (it depends on the frequencies only): the
-  // prefix P[o] of the owners' work (2 x 2 cell blocks, o = 0..NO) as 16-bit
-  // values, and the items of the steps of each thread's slice, step-major
-  const int NK = W * W, HB = T / 2, NO = HB * HB, NT = purify::kGridThreads;
-  c->chunk_tab_stride = purify::grid_tab_stride(T, J);
-  std::vector<uint16_t> tab((size_t)c->nchunks * c->chunk_tab_stride, 0);
-  std::vector<int> item_row(c->nchunks);
-  std::vector<uint32_t> items;
-  bool tab_overflow = c->chunk_max > (1 << purify::kItemEntryBits) || NO > 1024 || J > 8;
-  {
-    std::vector<int> off(NK + 1);
-    int64_t rows = 0;
-    for (int q = 0; q < c->nchunks && !tab_overflow; ++q) {
-      const int4 ch = chunks[q];
-      const int* kb = lkey.data() + ch.y;
-      const int ne = ch.z - ch.y;
-      // off[k] = first entry with start-cell key >= k (k = 0..NK)
-      for (int k = 0, e = 0; k <= NK; ++k) {
-        while (e < ne && kb[e] < k) ++e;
-        off[k] = e;
-      }
-      uint16_t* t = tab.data() + (size_t)q * c->chunk_tab_stride;
-      int acc = 0;
-      for (int o = 0; o < NO; ++o) {
-        t[o] = (uint16_t)acc;
-        const int R = 2 * (o / HB), C = 2 * (o % HB);
-        for (int kr = R; kr <= R + J; ++kr) acc += off[kr * W + C + J + 1] - off[kr * W + C];
-      }
-      t[NO] = (uint16_t)acc;
-      if (acc > 65535) {  // not reachable with chunk_max <= 864 (<= 25 owners per entry)
-        tab_overflow = true;
-        break;
-      }
-      // thread j walks steps [t0(j), t0(j + 1)) of the owners' concatenated runs
-      const int Wt = acc;
-      const int64_t nrow = (Wt + NT - 1) / NT;
-      item_row[q] = (int)rows;
-      items.resize((size_t)(rows + nrow) * NT, 0u);
-      uint32_t* dst = items.data() + (size_t)rows * NT;
-      rows += nrow;
-      auto t0_of = [&](int jj) { return (int)(((int64_t)jj * Wt + NT - 1) / NT); };
-      int jj = 0, tj0 = 0, tj1 = t0_of(1), tt = 0;
-      for (int o = 0; o < NO; ++o) {
-        const int R = 2 * (o / HB), C = 2 * (o % HB);
-        for (int kr = R; kr <= R + J; ++kr) {
-          for (int e = off[kr * W + C]; e < off[kr * W + C + J + 1]; ++e, ++tt) {
-            while (tt >= tj1) {
-              ++jj;
-              tj0 = tj1;
-              tj1 = t0_of(jj + 1);
-            }
-            const int kc = kb[e] - kr * W;  // start column, in [C, C + J]
-            dst[(size_t)(tt - tj0) * NT + jj] = purify::grid_item(e, R + J - kr, C + J - kc, o);
-          }
-        }
-      }
-    }
-    c->nitem_rows = rows;
-  }
-  if (tab_overflow || c->nitem_rows > INT32_MAX) {
+  const int T = c->tileT, NT = purify::kGridThreads;
+  // sort, tile lists, work units and the gather walk (host; gather_plan.cpp)
+  purify::GatherPlanParams prm{};
+  prm.M = M;
+  prm.L = c->L;
+  prm.J = c->J;
+  prm.T = T;
+  prm.fixed_bytes = purify::grid_fixed_bytes(T, c->J);
+  prm.entry_bytes = purify::grid_entry_bytes(c->J);
+  prm.smem_budget = purify::kGridSmemBudget;
+  prm.tab_stride = purify::grid_tab_stride(T, c->J);
+  prm.max_partials = kMaxPartials;
+  purify::GatherPlan plan;
+  const int prc = purify::build_gather_plan(reinterpret_cast<const int*>(k0.data()), prm, plan);
+  if (prc != 0) {
     cudaFree(d_uv_user);
     cudaFree(d_k0);
-    return PURIFY_E_SIZE;
+    return prc == -1 ? PURIFY_E_INVALID_ARG : PURIFY_E_SIZE;
   }
-  // degridding work units: each tile's home visibilities (a run of the sorted
-  // order) in chunks of at most dch; dch keeps the number of chunks (the grid
-  // of the kernel, whose FP64 partial sums use one slot per block) within
-  // kMaxPartials: at most ntiles + M / dch <= 16384 + 16384
-  const int64_t dch = std::max<int64_t>(1024, (2 * M + kMaxPartials - 1) / kMaxPartials);
-  std::vector<int4> dchunks;
-  for (int t = 0; t < c->ntiles; ++t) {
-    const int b = cnt[t], e = cnt[t + 1];
-    const int nc = (int)((e - b + dch - 1) / dch);
-    for (int k = 0; k < nc; ++k) {
-      const int cb = b + (int)((int64_t)(e - b) * k / nc), ce = b + (int)((int64_t)(e - b) * (k + 1) / nc);
-      dchunks.push_back(make_int4(t, cb, ce, 0));
-    }
-  }
-  std::stable_sort(dchunks.begin(), dchunks.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
-  c->ndchunks = (int)dchunks.size();
+  c->nlist = (int64_t)plan.list.size();
+  c->chunk_max = plan.chunk_max;
+  c->nchunks = (int)plan.chunks.size();
+  c->nslots = plan.nslots;
+  c->chunk_tab_stride = prm.tab_stride;
+  c->nitem_rows = plan.nitem_rows;
+  c->ndchunks = (int)plan.dchunks.size();
+  const int nslots = plan.nslots;
   if ((st = dev_alloc(&c->d_uv, M)) == PURIFY_OK && (st = dev_alloc(&c->d_perm, M)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_list, c->nlist)) == PURIFY_OK && (st = dev_alloc(&d_lk, c->nlist)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_chunks, c->nchunks)) == PURIFY_OK &&
@@ -476,24 +331,26 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       (st = dev_alloc(&c->d_tile_nchunk, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_tile_cnt, c->ntiles)) == PURIFY_OK &&
       (st = dev_alloc(&c->d_slots, (size_t)std::max(1, nslots) * T * T)) == PURIFY_OK) {
-    cudaMemcpyAsync(c->d_perm, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_perm, plan.perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, s);
     {
       std::vector<int2> lk(c->nlist);
-      for (int64_t e = 0; e < c->nlist; ++e) lk[e] = make_int2(list[e], lkey[e]);
+      for (int64_t e = 0; e < c->nlist; ++e) lk[e] = make_int2(plan.list[e], plan.lkey[e]);
       cudaMemcpyAsync(d_lk, lk.data(), c->nlist * sizeof(int2), cudaMemcpyHostToDevice, s);
       launch_gather_perm(M, d_uv_user, c->d_perm, c->d_uv, s);
       PURIFY_LAUNCH(c, "list_setup", s,
                     (k_list_setup<<<nblk(c->nlist), 256, 0, s>>>(d_lk, c->d_uv, c->ks, c->nlist, c->d_list)));
       if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
     }
-    cudaMemcpyAsync(c->d_chunks, chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_chunk_tab, tab.data(), tab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s);
-    if (!items.empty()) cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_item_row, item_row.data(), c->nchunks * sizeof(int), cudaMemcpyHostToDevice, s);
+    static_assert(sizeof(purify::PlanI4) == sizeof(int4), "plan work units have the layout of int4");
+    cudaMemcpyAsync(c->d_chunks, plan.chunks.data(), c->nchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_chunk_tab, plan.tab.data(), plan.tab.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s);
+    if (!plan.items.empty())
+      cudaMemcpyAsync(c->d_items, plan.items.data(), plan.items.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_item_row, plan.item_row.data(), c->nchunks * sizeof(int), cudaMemcpyHostToDevice, s);
     if (c->ndchunks > 0)
-      cudaMemcpyAsync(c->d_dchunks, dchunks.data(), c->ndchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_tile_slot0, slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c->d_tile_nchunk, nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(c->d_dchunks, plan.dchunks.data(), c->ndchunks * sizeof(int4), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_slot0, plan.slot0.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_tile_nchunk, plan.nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->d_tile_cnt, 0, c->ntiles * sizeof(unsigned), s);
     if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
   }

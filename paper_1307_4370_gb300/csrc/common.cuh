@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "purify.h"
+#include "gather_plan.h"
 
 namespace purify {
 
@@ -212,7 +213,6 @@ extern std::atomic<unsigned long long> g_launches;
 // bank conflicts); per CTA the prefix of the cell blocks' work and two
 // partial-sum slots per thread.
 namespace purify {
-constexpr int kGridThreads = 256;
 __host__ __device__ constexpr int grid_wstride(int J) { return 2 * (J + 2) + 1; }
 __host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 8 + 4 * (size_t)grid_wstride(J); }
 // The partial-sum slots share their space with the grid halo that the Gram
@@ -231,13 +231,6 @@ constexpr size_t kGridSmemBudget = 72 * 1024;
 // 16-bit per-chunk table of the gather: the NO + 1 owner-work prefix values
 // (stride rounded to 8 entries = 16 bytes)
 __host__ __device__ constexpr int grid_tab_stride(int T, int J) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }
-// One gather step of the gridding: a 32-bit item (entry index in the chunk,
-// padded row tap of the block's first cell row, padded column tap of its
-// first cell column, cell block), 12 + 4 + 4 + 10 bits.
-constexpr int kItemEntryBits = 12;
-__host__ __device__ constexpr uint32_t grid_item(int e, int ar, int bc, int o) {
-  return (uint32_t)e | ((uint32_t)ar << 12) | ((uint32_t)bc << 16) | ((uint32_t)o << 20);
-}
 }  // namespace purify
 
 struct purify_ctx {
