@@ -128,7 +128,12 @@ typedef struct {
  * frequencies, so it is set up once).  uv holds M float32 pairs and may be
  * a host or a device pointer; it is read during the call and not kept.
  * Set-up sorts the visibilities by grid tile and builds the tile lists of
- * the gridding adjoint; this call synchronises `stream`.
+ * the gridding adjoint and its stored gather walk (one 32-bit item per
+ * visibility and 2 x 2 cell block its footprint meets, about 12 per
+ * visibility for J = 6, so ~50 bytes of device memory per visibility besides
+ * the grids and tables); this call synchronises `stream`.  PURIFY_E_SIZE if a
+ * gridding work unit does not fit the walk's encoding (not reached for the
+ * supported sizes), PURIFY_E_ALLOC if device memory runs out.
  * *out receives the context, or NULL on failure. */
 int purify_create(purify_ctx** out, const purify_desc* desc, const float* uv,
                   purify_stream_t stream);
