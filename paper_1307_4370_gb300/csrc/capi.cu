@@ -505,6 +505,8 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   purify_ctx* c = new (std::nothrow) purify_ctx();
   if (!c) return PURIFY_E_ALLOC;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PURIFY_E_CUDA; }
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
+    c->sms = 1;
   c->n = d->n;
   c->L = 2 * d->n;
   c->J = d->J;

@@ -235,6 +235,7 @@ __host__ __device__ constexpr int grid_tab_stride(int T, int J) { return ((T / 2
 
 struct purify_ctx {
   int device;
+  int sms;               // streaming multiprocessors of the device
   int n, L, J, levels, q;
   int kernel;           // PURIFY_KERNEL_KB or PURIFY_KERNEL_GAUSS
   float2* d_tv;         // 7 N scratch of the TV prox (input, two dual pairs ping-ponged, last dual pair)

@@ -423,11 +423,23 @@ static void basis_layout(const purify_ctx* c, int& dirac_plane, int& plane0, Bas
   }
 }
 
-// Largest divisor of H that is at most kTile.
-static int tile_for(int H) {
-  for (int t = std::min(kTile, H); t > 1; --t)
-    if (H % t == 0) return t;
-  return 1;
+// Tile of one level: the largest divisor t <= kTile of H whose grid of
+// (H / t)^2 tiles per plane times `planes` gives every SM a CTA; failing
+// that, the largest divisor <= kMinTile (deep levels are small, and a CTA per
+// tile of a few coefficients only wastes its halo).  Every divisor of
+// H = 2^a or 3 * 2^a has the same form, as the index splits need.
+constexpr int kMinTile = 4;
+static int tile_for(int H, int64_t planes, int sms) {
+  int fallback = 1;
+  for (int t = std::min(kTile, H); t >= 1; --t) {
+    if (H % t != 0) continue;
+    if ((int64_t)(H / t) * (H / t) * planes >= (int64_t)sms) return t;
+    if (t <= kMinTile) {
+      fallback = t;
+      break;
+    }
+  }
+  return fallback;
 }
 
 // Finish zeta when the dictionary has no wavelet plane (Dirac only).
@@ -473,7 +485,7 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
   for (int lev = 0; lev < c->levels; ++lev) {
     const int L = c->n >> lev;
     const int H = L / 2;
-    const int TI = tile_for(H);
+    const int TI = tile_for(H, nb + (lev == 0 && dirac_plane >= 0 ? 1 : 0), c->sms);
     LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale, lev == 0, lev == 0 ? dirac_plane : -1};
     const float2* in = (lev == 0) ? x : c->d_ll[(lev - 1) & 1];
     float2* llo = c->d_ll[lev & 1];
@@ -507,7 +519,7 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
   for (int lev = c->levels - 1; lev >= 0; --lev) {
     const int L = c->n >> lev;  // output side
     const int H = L / 2;
-    const int TO = tile_for(H);
+    const int TO = tile_for(H, lev == 0 ? 1 : nb, c->sms);
     LevelGeom G{TO, c->n, L, nb, plane0, lev == 0, scale, 0, -1};
     const bool from_plane = (lev == c->levels - 1);
     const float2* llin = from_plane ? nullptr : c->d_ll[(lev + 1) & 1];
