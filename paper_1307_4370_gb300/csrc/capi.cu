@@ -245,18 +245,6 @@ __global__ void k_fill_f32(int64_t n, float* p, float v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
-__global__ void k_scatter_perm(int64_t n, const float2* __restrict__ src, const int* __restrict__ perm,
-                               float2* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[perm[i]] = src[i];
-}
-
-__global__ void k_gather_u32(int64_t n, const uint32_t* __restrict__ src, const int* __restrict__ perm,
-                             uint32_t* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = src[perm[i]];
-}
-
 __global__ void k_sqrt_to(const double* src, double* dst) { *dst = sqrt(*src); }
 
 unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
@@ -303,7 +291,7 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   prm.fixed_bytes = purify::grid_fixed_bytes(T, c->J);
   prm.entry_bytes = purify::grid_entry_bytes(c->J);
   prm.smem_budget = purify::kGridSmemBudget;
-  prm.tab_stride = purify::grid_tab_stride(T, c->J);
+  prm.tab_stride = purify::grid_tab_stride(T);
   prm.max_partials = kMaxPartials;
   purify::GatherPlan plan;
   const int prc = purify::build_gather_plan(reinterpret_cast<const int*>(k0.data()), prm, plan);

@@ -230,7 +230,7 @@ __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
 constexpr size_t kGridSmemBudget = 72 * 1024;
 // 16-bit per-chunk table of the gather: the NO + 1 owner-work prefix values
 // (stride rounded to 8 entries = 16 bytes)
-__host__ __device__ constexpr int grid_tab_stride(int T, int J) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }
+__host__ __device__ constexpr int grid_tab_stride(int T) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }
 }  // namespace purify
 
 struct purify_ctx {
