@@ -77,10 +77,13 @@ def test_deapodisation_profile():
 @pytest.mark.parametrize("J", [4, 6, 8])
 @pytest.mark.parametrize("f", [0.0, 0.05, 0.125, 0.25])
 def test_gauss_transform_matches_quadrature(J, f):
-    # g_hat is the transform of the untruncated Gaussian: integrate over R.
+    # g_hat is the transform of the untruncated Gaussian: integrate over R,
+    # as twice the integral over [0, t_max] with exp(-b t_max^2) = e^-80 (the
+    # rest of the tail is below 1e-35 of the value)
     b = kb.gauss_b(J)
-    val, _ = integrate.quad(lambda t: np.exp(-b * t * t) * np.cos(2 * np.pi * f * t), -np.inf, np.inf,
-                            epsabs=1e-15, epsrel=1e-14, limit=400)
+    t_max = np.sqrt(80.0 / b)
+    val, _ = integrate.quad(lambda t: 2.0 * np.exp(-b * t * t) * np.cos(2 * np.pi * f * t), 0.0, t_max,
+                            epsabs=0.0, epsrel=1e-13, limit=400)
     assert abs(kb.gauss_transform(f, J) - val) <= 1e-12 * abs(val)
 
 
