@@ -43,15 +43,18 @@ int build_gather_plan(const int* k0, const GatherPlanParams& prm, GatherPlan& ou
       for (int b = 0; b < (c1 != c0 ? 2 : 1); ++b) tl[nt++] = rs[a] * TD + cs[b];
     return nt;
   };
-  std::vector<int>& lcnt = out.list_off;
-  lcnt.assign(ntiles + 1, 0);
+  // (list positions are 32-bit on the device: at most 2^31 - 1 entries)
+  std::vector<int64_t> lcnt64(ntiles + 1, 0);
   int tl[4];
   for (int64_t si = 0; si < M; ++si) {
     const int nt = tiles_of(si, tl);
-    for (int k = 0; k < nt; ++k) lcnt[tl[k] + 1]++;
+    for (int k = 0; k < nt; ++k) lcnt64[tl[k] + 1]++;
   }
-  for (int t = 0; t < ntiles; ++t) lcnt[t + 1] += lcnt[t];
-  const int64_t nlist = lcnt[ntiles];
+  for (int t = 0; t < ntiles; ++t) lcnt64[t + 1] += lcnt64[t];
+  const int64_t nlist = lcnt64[ntiles];
+  if (nlist > 0x7fffffff) return -2;
+  std::vector<int>& lcnt = out.list_off;
+  lcnt.assign(lcnt64.begin(), lcnt64.end());
   out.list.resize(nlist);
   out.lkey.resize(nlist);
   {

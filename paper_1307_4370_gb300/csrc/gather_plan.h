@@ -73,8 +73,9 @@ struct GatherPlan {
   std::vector<PlanI4> dchunks;  // degridding units (tile, sorted begin, sorted end, 0), heavy first
 };
 
-// Returns 0, or -1 for invalid parameters, -2 when a chunk's gather table
-// does not fit its 16-bit / bit-field encoding.
+// Returns 0, or -1 for invalid parameters, -2 when the tile lists exceed
+// 2^31 - 1 entries or a chunk's gather table does not fit its 16-bit /
+// bit-field encoding.
 int build_gather_plan(const int* k0 /* M x 2: first footprint cell (row, column) in [0, L) */,
                       const GatherPlanParams& prm, GatherPlan& out);
 
