@@ -153,12 +153,19 @@ const char* purify_last_error(void);
  * (N float32, row-major like the image; host or device pointer), copied
  * into the context during the call; NULL restores B = I (every experiment
  * of §6).  Every later Phi, Phi^H, CG and SDMM call of this context applies
- * it; SDMM states re-capture their iteration graph on their next step.  Do
- * not call it while work of this context is in flight on other streams.  A
- * batch (purify_batch_create) keeps the beam its graphs were built with:
- * set the beam before creating the batch.  Synchronises `stream`.
+ * it; SDMM states, and batches holding one of them, re-capture their
+ * iteration graph on their next step.  Do not call it while work of this
+ * context is in flight on other streams.  Synchronises `stream`.
  * PURIFY_E_INVALID_ARG for a null context. */
 int purify_set_beam(purify_ctx* ctx, const float* beam, purify_stream_t stream);
+
+/* The l2 bound of problem eq. delta for i.i.d. complex Gaussian noise (§6):
+ * eps^2 = (2M + 4 sqrt(M)) sigma_n^2 / 2, the mean of the chi^2 distribution
+ * with 2M degrees of freedom plus two standard deviations, where
+ * sigma_n^2 / 2 is the variance of the real and of the imaginary part of the
+ * noise.  Host arithmetic (no device, no context); *eps receives the bound.
+ * PURIFY_E_INVALID_ARG for M < 1, sigma_n < 0 or a NULL eps. */
+int purify_l2_bound(int64_t M, double sigma_n, double* eps);
 
 /* Sizes of a context: N = n*n, M, q = number of bases, D = q*N. */
 int purify_sizes(const purify_ctx* ctx, int64_t* N, int64_t* M, int32_t* q,
@@ -371,8 +378,9 @@ int purify_sdmm_import(purify_ctx* ctx, purify_sdmm_state* st, const void* host_
  * context and state and of any sizes, advanced together.  §4.5 discusses
  * parallel evaluation of SDMM's independent parts; here whole problems run
  * side by side.  One batch iteration is one CUDA graph with one branch per
- * problem (captured at the first step, recaptured when a problem's cg_iters
- * or data format changes), so the kernels of the problems overlap on the GPU.
+ * problem (captured at the first step, recaptured when any problem's
+ * cg_iters, data format, prior, data blocks, beam or imported state changed
+ * since), so the kernels of the problems overlap on the GPU.
  * Contexts and states must be distinct, on one device, and already
  * initialised (purify_sdmm_init).  purify_batch_step runs `iters` iterations
  * of every problem on `stream`; each state can be read as usual afterwards.

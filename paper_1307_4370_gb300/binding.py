@@ -74,6 +74,7 @@ _SIGS = {
     "purify_sdmm_set_blocks": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "purify_sdmm_set_prior": (_i32, [_vp, _vp, _i32, _i32]),
     "purify_prox_tv": (_i32, [_vp, _vp, _vp, ctypes.c_float, _i32, _vp, _vp]),
+    "purify_l2_bound": (ctypes.c_int, [_i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "purify_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64)]),
     "purify_phi": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -474,8 +475,10 @@ class SdmmState:
 
 
 def l2_bound(M: int, sigma: float) -> float:
-    """eps = sqrt((2M + 4 sqrt M) sigma^2 / 2), the chi^2 bound of §6."""
-    return math.sqrt((2.0 * M + 4.0 * math.sqrt(M)) * sigma * sigma / 2.0)
+    """purify_l2_bound: the chi^2 bound eps of §6 for M visibilities with noise level sigma."""
+    out = ctypes.c_double()
+    _check("purify_l2_bound", load().purify_l2_bound(int(M), float(sigma), ctypes.byref(out)))
+    return out.value
 
 
 class Batch:

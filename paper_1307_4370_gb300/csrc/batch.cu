@@ -4,7 +4,9 @@
 // batch iteration is captured once as a single CUDA graph with one branch per
 // problem: the branches fork from one event and join into one, so a launch of
 // the graph runs one SDMM iteration (Algorithm 1 steps 5-9) of every problem,
-// and the GPU overlaps the small kernels of different problems.  (A
+// and the GPU overlaps the small kernels of different problems.  The graph
+// bakes in each state's buffers and options; a step re-captures it when a
+// state's graph key (step_graph_key) differs from the one it was built with.  (A
 // persistent kernel with software grid barriers between the phases was the
 // other candidate; on this GPU its barriers cost more than the graph's kernel
 // boundaries, so the batch is a graph.)
@@ -16,7 +18,7 @@ struct purify_batch {
   int device = -1;
   std::vector<purify_ctx*> ctxs;
   std::vector<purify_sdmm_state*> sts;
-  std::vector<int> keys;  // per problem: cg_iters * 2 + bf16 flag at capture time
+  std::vector<purify::GraphKey> keys;  // per problem: what its branch was captured with
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> done;
@@ -71,7 +73,7 @@ int capture(purify_batch* b) {
   }
   b->launches = (int)(g_launches.load(std::memory_order_relaxed) - l0);
   g_launches.fetch_sub((unsigned long long)b->launches, std::memory_order_relaxed);  // capture is not a launch
-  for (size_t i = 0; i < b->sts.size(); ++i) b->keys[i] = b->sts[i]->params.cg_iters * 2 + b->sts[i]->y_bf16;
+  for (size_t i = 0; i < b->sts.size(); ++i) b->keys[i] = step_graph_key(b->sts[i]);
   return PURIFY_OK;
 }
 
@@ -98,7 +100,7 @@ int purify_batch_create(purify_batch** out, purify_ctx* const* ctxs, purify_sdmm
   if (prev != b->device) cudaSetDevice(b->device);
   b->ctxs.assign(ctxs, ctxs + count);
   b->sts.assign(states, states + count);
-  b->keys.assign(count, -1);
+  b->keys.assign(count, purify::GraphKey{});
   b->branch.assign(count, nullptr);
   b->done.assign(count, nullptr);
   int rc = check_cuda(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
@@ -125,7 +127,8 @@ int purify_batch_step(purify_batch* b, int32_t iters, purify_stream_t stream) {
   int rc = PURIFY_OK;
   bool stale = !b->exec;
   for (size_t i = 0; i < b->sts.size(); ++i)
-    if (b->keys[i] != b->sts[i]->params.cg_iters * 2 + b->sts[i]->y_bf16) stale = true;
+    if (b->keys[i] != step_graph_key(b->sts[i])) stale = true;  // cg_iters, data format, prior,
+                                                                 // blocks, beam or an import changed
   if (stale) rc = capture(b);
   cudaStream_t s = (cudaStream_t)stream;
   for (int k = 0; rc == PURIFY_OK && k < iters; ++k) {

@@ -50,6 +50,10 @@ struct DeviceGuard {
 
 #define TRY_CUDA(expr) TRY(check_cuda(expr))
 
+// Device (or managed) memory that the current device may dereference: device
+// memory must belong to the current device (every call makes the context's
+// device current first), so a buffer of another GPU is rejected instead of
+// being read through peer access or faulting.
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -57,7 +61,14 @@ bool is_device_ptr(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == cur;
 }
 
 template <class T>
@@ -437,6 +448,15 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   return PURIFY_OK;
 }
 
+GraphKey step_graph_key(const purify_sdmm_state* st) {
+  GraphKey k;
+  k.cg_iters = st->params.cg_iters;
+  k.y_bf16 = st->y_bf16;
+  k.shape = st->shape_version;
+  k.beam = st->ctx->beam_version;
+  return k;
+}
+
 }  // namespace purify
 
 namespace {
@@ -578,6 +598,13 @@ int purify_set_beam(purify_ctx* c, const float* beam, purify_stream_t stream) {
     c->beam_on = true;
   }
   c->beam_version++;
+  return PURIFY_OK;
+}
+
+int purify_l2_bound(int64_t M, double sigma_n, double* eps) {
+  if (!eps || M < 1 || !(sigma_n >= 0.0)) return PURIFY_E_INVALID_ARG;
+  const double m = (double)M;
+  *eps = std::sqrt((2.0 * m + 4.0 * std::sqrt(m)) * sigma_n * sigma_n / 2.0);
   return PURIFY_OK;
 }
 
@@ -831,6 +858,7 @@ int purify_sdmm_set_prior(purify_ctx* c, purify_sdmm_state* st, int32_t prior, i
     TRY(tv_scratch_ready(c, &scr));
   }
   drop_graph(st);
+  st->shape_version++;  // batches that captured this state re-capture
   st->prior = prior;
   st->fgp_iters = prior == PURIFY_PRIOR_TV ? fgp_iters : 0;
   return PURIFY_OK;
@@ -857,6 +885,7 @@ int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, cons
   cudaStream_t s = (cudaStream_t)stream;
   TRY_CUDA(cudaStreamSynchronize(s));
   drop_graph(st);  // the iteration changes shape: re-capture on the next step
+  st->shape_version++;  // (and so do batches that captured this state)
   void* old[] = {st->d_block_of, st->d_pos, st->d_bchunks, st->d_beps, st->d_bscale};
   for (void* p : old)
     if (p) cudaFree(p);
@@ -907,8 +936,8 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
   if (!st->params.use_graph || c->prof.on) {
     TRY(enqueue_sdmm_step(c, st, s));
   } else {
-    const int key = st->params.cg_iters * 2 + st->y_bf16;
-    if (!st->step_exec || st->graph_cg_iters != key || st->graph_beam != c->beam_version) {
+    const GraphKey key = step_graph_key(st);
+    if (!st->step_exec || st->graph_key != key) {
       TRY(drop_graph(st));
       if (!st->cap_stream) TRY_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
       TRY_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -926,8 +955,7 @@ int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t strea
         st->step_exec = nullptr;
         return PURIFY_E_CUDA;
       }
-      st->graph_cg_iters = key;
-      st->graph_beam = c->beam_version;
+      st->graph_key = key;
       g_launches.fetch_sub((unsigned long long)st->launches_per_step, std::memory_order_relaxed);  // capture only
     }
     TRY_CUDA(cudaGraphLaunch(st->step_exec, s));
@@ -1094,6 +1122,7 @@ int purify_sdmm_import(purify_ctx* c, purify_sdmm_state* st, const void* host_bu
   st->iters = h.iters;
   st->eps = h.eps;
   st->y_bf16 = 0;
+  st->shape_version++;
   return check_cuda(cudaStreamSynchronize(s));
 }
 

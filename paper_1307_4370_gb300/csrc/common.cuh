@@ -331,6 +331,21 @@ inline void prof_stop(purify_ctx* c, const char* name, cudaStream_t s, size_t i)
     purify::prof_stop((ctx), (name), (stream), _pi);          \
   } while (0)
 
+namespace purify {
+// What a captured SDMM step depends on besides the state's fixed buffers: a
+// graph whose key differs from the state's current key must be re-captured.
+struct GraphKey {
+  int cg_iters = -1;
+  int y_bf16 = 0;
+  int shape = -1;  // purify_sdmm_state::shape_version
+  int beam = -1;   // purify_ctx::beam_version
+  bool operator==(const GraphKey& o) const {
+    return cg_iters == o.cg_iters && y_bf16 == o.y_bf16 && shape == o.shape && beam == o.beam;
+  }
+  bool operator!=(const GraphKey& o) const { return !(*this == o); }
+};
+}  // namespace purify
+
 struct purify_sdmm_state {
   purify_ctx* ctx;
   // image-size vectors
@@ -372,8 +387,9 @@ struct purify_sdmm_state {
   float* d_bscale;          // R projection factors min(1, eps_i / ||a_i - y_i||)
   int prior;                // PURIFY_PRIOR_SARA or PURIFY_PRIOR_TV
   int fgp_iters;            // TV prox inner iterations
-  int graph_cg_iters;       // key of the captured graph (cg_iters, data format)
-  int graph_beam;           // beam version of the context when it was captured
+  int shape_version;        // bumped by every call that changes what one step launches or the
+                            // buffers its kernels read (prior, blocks, data format, import)
+  purify::GraphKey graph_key;  // key of the captured per-state graph
   int launches_per_step;    // kernels in one captured step
 };
 
@@ -382,6 +398,7 @@ namespace purify {
 // Launchers (implemented in the .cu files).
 int check_cuda(cudaError_t e);
 int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s);  // capi.cu
+GraphKey step_graph_key(const purify_sdmm_state* st);                          // capi.cu
 
 // nufft.cu
 // kRowInCgUpd: apply the pending CG vector update, then transform r;

@@ -16,7 +16,10 @@
 // two calls that overlap on the GPU (different streams, or different host
 // threads) race on it and give wrong results; order them on one stream.
 // The first call on a device looks up the array's device address with that
-// device current; make that first call before any stream capture.
+// device current; make that first call before any stream capture.  The
+// array keeps the twiddles and deapodisation factors of the last (n, J) used
+// on the device: a call of another size rewrites them (on its stream) before
+// its transforms read them, a call of the same size reuses them.
 //
 // The arithmetic is that of purify_phi (§5 eq. opmodel with B = I): the same
 // deapodisation, zero padding, unitary DFT and Kaiser-Bessel interpolation;
@@ -45,17 +48,20 @@ constexpr size_t kStaticBytes = kGridBytes + kHalfBytes + kTwBytes + kDzBytes;
 // The scratch array (its host-side name is not a device address).
 __device__ __align__(256) unsigned char g_phi_scratch[kStaticBytes];
 
-// Device address of g_phi_scratch per device, looked up once per device.
+// Device address of g_phi_scratch per device, looked up once per device,
+// and the (n, J) whose twiddles and deapodisation factors that device's
+// array holds (0 = none yet), so repeated calls of one size skip the tables.
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];
+int g_table_key[kMaxDevices];
 std::mutex g_scratch_mu;
 
-int scratch_address(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return PURIFY_E_CUDA;
-  }
+// Fitted tap polynomials per kernel support J (they do not depend on n).
+KbPoly g_kb[kMaxJ + 1];
+bool g_kb_ready[kMaxJ + 1];
+
+int scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return PURIFY_E_CUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
@@ -220,13 +226,16 @@ __global__ void k_static_degrid(const float2* __restrict__ X, const float2* __re
   }
 }
 
-bool is_dev(const void* p) {
+// Managed memory, or device memory of the current device (the one whose copy
+// of the scratch array the call uses); another GPU's buffer is rejected.
+bool is_dev(const void* p, int dev) {
   cudaPointerAttributes a;
   if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 template <int EPT>
@@ -257,9 +266,14 @@ extern "C" int purify_phi_static(int32_t n, int32_t J, int64_t M, const float* u
     while (r % 3 == 0) { r /= 3; ++threes; }
     if (threes > 1) return PURIFY_E_UNSUPPORTED;
   }
-  if (!is_dev(uv) || !is_dev(x) || !is_dev(y)) return PURIFY_E_NOT_DEVICE_PTR;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PURIFY_E_CUDA;
+  }
+  if (!is_dev(uv, dev) || !is_dev(x, dev) || !is_dev(y, dev)) return PURIFY_E_NOT_DEVICE_PTR;
   void* base = nullptr;
-  const int rc = scratch_address(&base);
+  const int rc = scratch_address(dev, &base);
   if (rc != PURIFY_OK) return rc;
   unsigned char* b = static_cast<unsigned char*>(base);
   float2* X = reinterpret_cast<float2*>(b);
@@ -268,12 +282,26 @@ extern "C" int purify_phi_static(int32_t n, int32_t J, int64_t M, const float* u
   float* dz = reinterpret_cast<float*>(b + kGridBytes + kHalfBytes + kTwBytes);
   cudaStream_t s = (cudaStream_t)stream;
   const double beta = st_beta(J), i0b = std::cyl_bessel_i(0.0, beta);
-  k_static_tables<<<(L + 255) / 256, 256, 0, s>>>(n, L, J, beta, i0b, tw, dz);
+  KbPoly kb;
+  {
+    // the tables in the array are rewritten only when (n, J) changes on this
+    // device; the polynomials are fitted once per J in the process
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    const int key = n * 16 + J;
+    if (g_table_key[dev] != key) {
+      k_static_tables<<<(L + 255) / 256, 256, 0, s>>>(n, L, J, beta, i0b, tw, dz);
+      if (cudaGetLastError() != cudaSuccess) return PURIFY_E_CUDA;
+      g_table_key[dev] = key;
+    }
+    if (!g_kb_ready[J]) {
+      st_fit(J, g_kb[J]);
+      g_kb_ready[J] = true;
+    }
+    kb = g_kb[J];
+  }
   const int frc = (L % 3 == 0) ? st_fft<12>((const float2*)x, half, X, dz, tw, plan, n, s)
                                : st_fft<8>((const float2*)x, half, X, dz, tw, plan, n, s);
   if (frc != PURIFY_OK) return frc;
-  KbPoly kb;
-  st_fit(J, kb);
   const double sc = (double)L / (2.0 * M_PI);
   KappaScale ks{(float)sc, (float)(sc - (double)(float)sc)};
   const unsigned blocks = (unsigned)std::min<int64_t>((M + 255) / 256, 4096);

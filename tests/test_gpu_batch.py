@@ -104,3 +104,84 @@ def test_batch_with_mixed_forms():
             st.step()
         assert rel_err(xb[k], host(st.get_image())) <= 1e-6
     batch.close()
+
+
+def test_batch_recaptures_after_state_changes():
+    """A batch step after purify_sdmm_set_blocks / set_prior / set_data_bf16 on
+    one of its states must run the new form of that problem (its graph is
+    re-captured), matching the problem stepped on its own."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    probs = [make(s) for s in SPECS[:2]]
+
+    def fresh(w, p, y, eps):
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+        st = ctx.sdmm_state()
+        st.init(dev(y, torch), eps)
+        return ctx, st
+
+    made = [fresh(*pr) for pr in probs]
+    batch = binding.Batch([st for _, st in made])
+    batch.step(2)
+    # change the form of every problem between batch steps
+    w0, p0, y0, eps0 = probs[0]
+    made[0][1].set_blocks([0, w0.M // 2, w0.M], [eps0 * 0.7, eps0 * 0.75])
+    made[1][1].set_prior("tv", fgp_iters=8)
+    made[1][1].init(dev(probs[1][2], torch), probs[1][3])   # the prior is chosen before init
+    batch.step(2)
+    w1, p1, y1, eps1 = probs[1]
+    made[1][1].set_data_bf16(dev(y1, torch))
+    batch.step(1)
+    torch.cuda.synchronize()
+    xb = [host(st.get_image()) for _, st in made]
+    # the same sequence, stepped problem by problem
+    solo = [fresh(*pr) for pr in probs]
+    for _ in range(2):
+        for _, st in solo:
+            st.step()
+    solo[0][1].set_blocks([0, w0.M // 2, w0.M], [eps0 * 0.7, eps0 * 0.75])
+    solo[1][1].set_prior("tv", fgp_iters=8)
+    solo[1][1].init(dev(probs[1][2], torch), probs[1][3])
+    for _ in range(2):
+        for _, st in solo:
+            st.step()
+    solo[1][1].set_data_bf16(dev(y1, torch))
+    for _, st in solo:
+        st.step()
+    for k in range(2):
+        assert rel_err(xb[k], host(solo[k][1].get_image())) <= 1e-6
+    batch.close()
+
+
+def test_batch_with_the_largest_batched_sizes():
+    """A batch holding an n = 384 problem (768 x 768 grid, radix 3) and an
+    n = 512 one, the two largest image sides of the 32-problem workload: each
+    follows its solo iterates, and the n = 384 one matches the FP64 oracle."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    iters = 3
+    probs = [make(s) for s in [(384, 40000, 6, 21), (512, 80000, 4, 22)]]
+    made = []
+    for w, p, y, eps in probs:
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+        st = ctx.sdmm_state()
+        st.init(dev(y, torch), eps)
+        made.append((ctx, st))
+    batch = binding.Batch([st for _, st in made])
+    batch.step(iters)
+    torch.cuda.synchronize()
+    xb = [host(st.get_image()) for _, st in made]
+    for k, (w, p, y, eps) in enumerate(probs):
+        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+        st = ctx.sdmm_state()
+        st.init(dev(y, torch), eps)
+        for _ in range(iters):
+            st.step()
+        assert rel_err(xb[k], host(st.get_image())) <= 1e-6
+    w, p, y, eps = probs[0]
+    ref = osdmm.solve(simulate.operators(p.uv, w.n, w.J), y, eps, (w.n, w.n), (9, w.n, w.n),
+                      iters=iters, cg_iters=w.cg_iters)
+    assert rel_err(xb[0], ref.x_hat) <= 1e-4
+    batch.close()

@@ -181,10 +181,28 @@ def test_profiler_and_launch_counter():
     assert all(r[2] > 0 for r in prof)
 
 
+def golden(name):
+    """Stored FP64-oracle results of a full-size run (tests/golden/make_golden.py)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".npz")
+    return dict(np.load(path))
+
+
+def sampled_errors(x, rep, g):
+    """Errors of a GPU run against a stored oracle run: image on the pixel
+    sample and in norm, nu and f1 of the last iteration (relative)."""
+    xs = np.asarray(x).ravel()
+    return {"x_hat_sample": rel_err(xs[g["idx"]], g["x"]),
+            "x_hat_norm": abs(np.linalg.norm(xs) - float(g["x_norm"])) / float(g["x_norm"]),
+            "nu": abs(rep["nu"] - float(g["nu"])) / float(g["nu"]),
+            "f1": abs(rep["f1"] - float(g["f1"])) / float(g["f1"])}
+
+
 def test_mixed_precision_full_size_errors(capsys):
-    """1024 x 1024, M = 2^21 with radial arcs: two SDMM iterations (2 CG steps)
-    with complex64 data and with bf16-stored data, each against the FP64 oracle;
-    the error of every output is printed (recorded in the design notes)."""
+    """1024 x 1024, M = 2^21 with radial arcs, the benchmark's configuration:
+    two SDMM iterations of 10 CG steps with complex64 data and with bf16-stored
+    data, each against the FP64 oracle (stored run); the error of every output
+    is printed (recorded in the design notes)."""
     torch = require_gpu()
     from paper_1307_4370_gb300 import binding
 
@@ -192,25 +210,73 @@ def test_mixed_precision_full_size_errors(capsys):
     w = p.workload
     y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, w.isnr_db)
     y = y.astype(np.complex64).astype(np.complex128)
-    iters, cg_iters = 2, 2
-    ops = simulate.operators(p.uv, w.n, w.J)
-    ref = osdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=iters, cg_iters=cg_iters)
+    g = golden("sdmm1024_k10")
+    assert int(g["t"]) == 2
     ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
     errs = {}
     for mode in ("c64", "bf16"):
         st = ctx.sdmm_state()
-        st.init(dev(y, torch), eps, cg_iters=cg_iters)
+        st.init(dev(y, torch), eps, cg_iters=10)
         if mode == "bf16":
             st.set_data_bf16(dev(y, torch))
-        for _ in range(iters):
+        for _ in range(2):
             st.step()
-        x = host(st.get_image())
-        rep = st.report()
-        errs[mode] = {"x_hat": rel_err(x, ref.x_hat),
-                      "nu": abs(rep["nu"] - ref.history[-1]["nu"]) / ref.history[-1]["nu"],
-                      "f1": abs(rep["f1"] - ref.history[-1]["f1"]) / ref.history[-1]["f1"]}
+        errs[mode] = sampled_errors(host(st.get_image()), st.report(), g)
+        if mode == "c64":
+            assert st.report()["gamma"] == pytest.approx(float(g["gamma"]), rel=1e-5)
     with capsys.disabled():
-        print("\nsdmm1024 errors vs FP64 oracle:", errs)
-    assert errs["c64"]["x_hat"] <= 1e-4
-    assert errs["bf16"]["x_hat"] <= 1e-2
+        print("\nsdmm1024 (2 iterations, k = 10) errors vs FP64 oracle:", errs)
+    assert errs["c64"]["x_hat_sample"] <= 1e-4 and errs["c64"]["x_hat_norm"] <= 1e-4
     assert errs["c64"]["nu"] <= 1e-4 and errs["c64"]["f1"] <= 1e-4
+    assert errs["bf16"]["x_hat_sample"] <= 1e-2
+
+
+def test_sdmm256_two_rounds_full_size(capsys):
+    """256 x 256, M = 65536 (the FP32 workload): 60 iterations of 10 CG steps
+    across one reweighting round (2 rounds x 30), against the stored FP64
+    oracle run; image, nu and f1 errors printed."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p, y, eps = problem("sdmm256")
+    w = p.workload
+    g = golden("sdmm256_rounds")
+    assert int(g["t"]) == 60
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    x, rep = ctx.sdmm_solve(dev(y, torch), eps, max_iters=30, cg_iters=10, rounds=2)
+    errs = sampled_errors(host(x), rep, g)
+    with capsys.disabled():
+        print("\nsdmm256 (2 rounds x 30 iterations, k = 10) errors vs FP64 oracle:", errs)
+    assert rep["iters"] == 60
+    assert errs["x_hat_sample"] <= 1e-4 and errs["x_hat_norm"] <= 1e-4
+    assert errs["nu"] <= 1e-4 and errs["f1"] <= 1e-4
+
+
+def test_halting_rule_stops_where_the_oracle_stops():
+    """purify_sdmm_solve with the halting test of §4.4 checked after every
+    iteration stops at the iteration where the FP64 oracle's solve(stop=True)
+    stops, with zeta, nu and the image matching.  The problem is chosen so
+    that zeta crosses xi = 1e-3 with a wide margin (2.2e-3 -> 2.7e-4) and nu
+    sits well inside [0.9, 1.1], so FP32 rounding cannot move the decision."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    p, y, eps = problem(inputs.Workload("h32", n=32, M=900, J=4, n_src=6, diffuse=False, seed=10))
+    w = p.workload
+    ref = osdmm.solve(simulate.operators(p.uv, w.n, w.J), y, eps, (w.n, w.n), (9, w.n, w.n),
+                      iters=200, cg_iters=10, stop=True)
+    last = ref.history[-1]
+    assert ref.t < 200 and osdmm.halted(last) and not osdmm.halted(ref.history[-2])
+    ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+    x, rep = ctx.sdmm_solve(dev(y, torch), eps, max_iters=200, cg_iters=10, check_every=1)
+    assert rep["iters"] == ref.t
+    assert abs(rep["zeta"] - last["zeta"]) <= 1e-5
+    assert rep["nu"] == pytest.approx(last["nu"], rel=1e-4)
+    assert rel_err(host(x), ref.x_hat) <= 1e-4
+    # checked every 11 iterations: the check at 11 does not halt, the one at 22 does
+    assert not osdmm.halted(ref.history[10]) and ref.t == 22
+    _, rep11 = ctx.sdmm_solve(dev(y, torch), eps, max_iters=200, cg_iters=10, check_every=11)
+    assert rep11["iters"] == 22
+    # a round shorter than the halting iteration runs to its end
+    _, rep21 = ctx.sdmm_solve(dev(y, torch), eps, max_iters=21, cg_iters=10, check_every=1)
+    assert rep21["iters"] == 21

@@ -269,3 +269,76 @@ def test_tv_reweighting_rule():
     delta = 1e-2 * g.max()
     assert np.allclose(w, delta / (delta + g), rtol=1e-15, atol=0)
     assert np.all(sdmm.reweight_tv(np.ones((4, 4)), 1) == 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Reweighting rule (§3.3, reading c14) and halting test (§4.4), pinned by
+# hand-computed values rather than by the rule restated.
+# ---------------------------------------------------------------------------
+def _identity_planes_ops(scales):
+    """Psi^H x = [s_0 x; s_1 x; ...] (planes in order), so alpha is known by hand."""
+    return sdmm.Operators(phi=None, phi_adj=None,
+                          psi_adj=lambda x: np.stack([s * x for s in scales]),
+                          psi=None)
+
+
+def test_reweight_hand_values():
+    # |alpha| = (0, 1, 2, 4) in plane 0; max 4
+    x = np.array([[0.0, 1.0], [-2.0, 4.0j]])
+    ops = _identity_planes_ops([1.0])
+    # round 1: delta = 0.4 -> 1, 2/7, 1/6, 1/11
+    assert np.allclose(sdmm.reweight(ops, x, 1)[0], [[1.0, 2 / 7], [1 / 6, 1 / 11]], rtol=1e-15, atol=0)
+    # round 2: delta = 0.04 -> 1, 1/26, 1/51, 1/101
+    assert np.allclose(sdmm.reweight(ops, x, 2)[0], [[1.0, 1 / 26], [1 / 51, 1 / 101]], rtol=1e-15, atol=0)
+    # round 7: 10^-7 * 4 is below the floor 1e-6 * 4 = 4e-6 -> delta = 4e-6
+    d = 4e-6
+    assert np.allclose(sdmm.reweight(ops, x, 7)[0], [[1.0, d / (d + 1)], [d / (d + 2), d / (d + 4)]],
+                       rtol=1e-15, atol=0)
+    # round 6 is exactly at the floor (10^-6 = 1e-6): same weights as round 7
+    assert np.allclose(sdmm.reweight(ops, x, 6), sdmm.reweight(ops, x, 7), rtol=1e-15, atol=0)
+    # weights are 1 where alpha = 0 and never exceed 1
+    w = sdmm.reweight(ops, x, 3)
+    assert w[0, 0, 0] == 1.0 and np.all(w <= 1.0)
+
+
+def test_reweight_zero_image_and_plane_order():
+    ops = _identity_planes_ops([1.0, 3.0])
+    assert np.all(sdmm.reweight(ops, np.zeros((3, 3)), 1) == 1.0)
+    # two planes: |alpha| = (1, 3) at one pixel, max 3; round 1: delta = 0.3
+    x = np.zeros((2, 2), dtype=complex)
+    x[1, 0] = 1.0
+    w = sdmm.reweight(ops, x, 1)
+    assert w.shape == (2, 2, 2)
+    assert w[0, 1, 0] == pytest.approx(0.3 / 1.3, rel=1e-15)
+    assert w[1, 1, 0] == pytest.approx(0.3 / 3.3, rel=1e-15)
+    w[0, 1, 0] = w[1, 1, 0] = 1.0
+    assert np.all(w == 1.0)
+
+
+@pytest.mark.parametrize("zeta,nu,expect", [
+    (0.5e-3, 1.0, True),        # inside the band, small change
+    (1e-3, 1.0, False),         # zeta = xi is not below xi
+    (0.999e-3, 0.9, True),      # nu = 1 - tau: band is closed
+    (0.999e-3, 1.1, True),      # nu = 1 + tau
+    (0.5e-3, 0.8999, False),    # below the band
+    (0.5e-3, 1.1001, False),    # above the band
+    (np.inf, 1.0, False),       # first iteration: f1(t-1) = 0
+    (0.0, 1.05, True),
+])
+def test_halted_truth_table(zeta, nu, expect):
+    assert sdmm.halted({"zeta": zeta, "nu": nu}) is expect
+
+
+def test_halted_stops_solve_at_first_true_record():
+    # the solve loop must stop right after the first iteration whose record halts
+    p = inputs.make_problem(inputs.Workload("h32", n=32, M=900, J=4, n_src=6, diffuse=False, seed=8))
+    w = p.workload
+    y, eps = simulate.visibilities(p.x_true, p.uv, w.J, p.noise_unit, 30.0)
+    ops = simulate.operators(p.uv, w.n, w.J)
+    free = sdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=200, cg_iters=10)
+    first = next((h["t"] for h in free.history if sdmm.halted(h)), None)
+    assert first is not None and first < 200
+    stopped = sdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=200, cg_iters=10, stop=True)
+    assert stopped.t == first
+    exact = sdmm.solve(ops, y, eps, (w.n, w.n), (9, w.n, w.n), iters=first, cg_iters=10)
+    assert np.array_equal(stopped.x_hat, exact.x_hat)
