@@ -262,7 +262,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_twp[0], c->d_twp[1], c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -531,6 +531,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   c->ks.lo = (float)(sc - (double)c->ks.hi);
   c->plan = make_plan(c->L);
   if (c->plan.nst < 0) { delete c; return PURIFY_E_UNSUPPORTED; }
+  c->fft_engine = (c->L >= 256 && c->L <= 4096 && (c->L & (c->L - 1)) == 0) ? 1 : 0;
   make_daubechies(c->wf);
   if (d->tile != 0) {
     c->tileT = d->tile;
@@ -572,6 +573,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
     // dz and tw are pageable host vectors: finish the copies before they go out of scope
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PURIFY_E_CUDA);
   }
+  if ((st = fft_prepare(c)) != PURIFY_OK) return fail(st);
   if ((st = setup_visibilities(c, uv, s)) != PURIFY_OK) return fail(st);
   // shared memory above 48 KB needs an opt-in per kernel; sizes here stay below it
   *out = c;

@@ -72,6 +72,14 @@ __device__ __forceinline__ void kb_weights(const KbPoly& kb, float x, float* w) 
   }
 }
 
+// floor(k / d) for 0 <= k < 2^16 and 1 <= d <= 128 from the rounded
+// reciprocal r = 1/d: (k + 1/2) r lies at least 1/(2d) from an integer and
+// its rounding error is below 2^-22 (k + 1/2)/d, so truncation is exact
+// (checked exhaustively over that range by a host test).
+__device__ __forceinline__ int quot_small(int k, float r) {
+  return __float2int_rz(__fmul_rn(__fadd_rn((float)k, 0.5f), r));
+}
+
 __device__ __forceinline__ int wrap(int k, int L) {
   k %= L;
   return k < 0 ? k + L : k;
@@ -253,6 +261,8 @@ struct purify_ctx {
 
   float* d_deapod;      // n: 1 / g_hat((r - n/2) / 2n)
   float2* d_tw;         // L: exp(-2 pi i m / L)
+  int fft_engine;       // 1: compile-time power-of-two engine (L = 256 .. 4096), 0: generic Stockham
+  float2* d_twp[2];     // per-stage twiddle tables of the power-of-two engine (8 and 16 per thread)
 
   // visibility table (sorted by grid tile of the first footprint cell)
   float2* d_uv;         // M sorted frequencies
@@ -434,6 +444,7 @@ struct RowOutArgs {
 
 // cg_j: in the CG modes, the CG step whose update this pass applies (its
 // inner-product partials are in the kCntDot slot).
+int fft_prepare(purify_ctx* c);  // tables of the power-of-two FFT engine (at context creation)
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j = 0);
 int cg_partial_blocks(const purify_ctx* c);
 // CG step sizes formed by the consuming kernels (few partials) or by a

@@ -36,13 +36,14 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
     if (i < ch.z) uq[q] = __ldg(&uv[i]);
   }
   // halo of the tile: eight cells per thread per round, all loads issued first
+  const float inv_w = 1.0f / (float)W;
   for (int k0 = 0; k0 < NW; k0 += 8 * NT) {
     float2 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = k0 + threadIdx.x + q * NT;
       if (k < NW) {
-        const int rr = k / W, cc = k - rr * W;  // W = T + J - 1 is not a Div form
+        const int rr = quot_small(k, inv_w), cc = k - rr * W;  // W = T + J - 1 <= 71, k < 2^13
         int r = R0 + rr, c = C0 + cc;
         if (r >= L) r -= L;
         if (c >= L) c -= L;
@@ -163,13 +164,6 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // chunk order.  Every cell is written once and the result does not depend
 // on scheduling.
 // ---------------------------------------------------------------------------
-// floor(k / d) for 0 <= k < 2^16 and 1 <= d <= 128 from the rounded
-// reciprocal r = 1/d: (k + 1/2) r lies at least 1/(2d) from an integer and
-// its rounding error is below 2^-22 (k + 1/2)/d, so truncation is exact
-// (checked exhaustively over that range by a host test).
-__device__ __forceinline__ int quot_small(int k, float r) {
-  return __float2int_rz(__fmul_rn(__fadd_rn((float)k, 0.5f), r));
-}
 
 struct Acc4 {  // a 2 x 2 block of complex sums
   float2 a00, a01, a10, a11;

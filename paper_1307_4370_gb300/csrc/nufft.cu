@@ -8,10 +8,13 @@
 //           k_row_inv   inverse row DFTs, crop Z^T, D and B, with fused
 //                       epilogues for the CG operator Q = Phi^H Phi + 2I and
 //                       the SDMM step.
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_p2.cuh"
 #include "reduce.cuh"
 
 namespace purify {
@@ -355,10 +358,236 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half
 }
 
 // ---------------------------------------------------------------------------
+// The same four passes on power-of-two grids (L = 256 .. 4096) with the
+// compile-time engine of fft_p2.cuh: the zero padding of the forward passes
+// and the crop of the adjoint ones prune the first / last stage.
+// ---------------------------------------------------------------------------
+template <int L>
+struct P2Cfg {
+  static constexpr int E = L >= 1024 ? 16 : 8;                     // plain row, column and inverse row passes
+  static constexpr int E_CG = 8;                                   // forward row pass with the CG update
+  static constexpr int NS_ROW = 256 / (L / E) > 0 ? 256 / (L / E) : 1;
+  static constexpr int NS_ROWCG = 256 / (L / E_CG) > 0 ? 256 / (L / E_CG) : 1;
+  static constexpr int NS_RINV = 512 / (L / E) > 0 ? (512 / (L / E) > 8 ? 8 : 512 / (L / E)) : 1;
+  static constexpr int NS_COL = 4;
+};
+
+template <int L, int E, int NSIG, int MODE>
+__global__ void __launch_bounds__(NSIG * L / E) k_row_fwd_p2(RowInArgs a, float2* __restrict__ half,
+                                                             const float* __restrict__ dz,
+                                                             const float* __restrict__ beam,
+                                                             const float2* __restrict__ twt, int n, DevScalars* sc,
+                                                             const double* __restrict__ cgpart, int cg_nblk,
+                                                             int cg_j) {
+  extern __shared__ float2 sm[];
+  RowFwdSrc<MODE> src;
+  src.a = a;
+  src.dz = dz;
+  src.beam = beam;
+  src.n = n;
+  src.L = L;
+  src.r0 = blockIdx.x * NSIG;
+  src.invL = 1.0f / (float)L;
+  src.alpha = src.beta = 0.f;
+  src.first = false;
+  src.cgpart = cgpart;
+  src.cg_nblk = cg_nblk;
+  src.cg_j = cg_j;
+  src.sc = sc;
+  if constexpr (MODE != kRowInPlain) {
+    const CgStep st = cg_consume(cgpart, cg_nblk, cg_j, sc);
+    src.alpha = st.alpha;
+    src.beta = st.beta;
+    src.first = st.first;
+  }
+  RowStoreDst dst{half + (size_t)src.r0 * L, L};
+  fft_p2<L, E, NSIG, false, true, false>(sm, twt, src, dst);
+}
+
+template <int L, int E, int NSIG>
+__global__ void __launch_bounds__(NSIG * L / E) k_col_fwd_p2(const float2* __restrict__ half, float2* __restrict__ X,
+                                                             const float2* __restrict__ twt, int n) {
+  extern __shared__ float2 sm[];
+  const int c0 = blockIdx.x * NSIG;
+  ColFwdSrc src{half, n, L, c0};
+  ColStoreDst dst{X, L, c0};
+  fft_p2<L, E, NSIG, true, true, false>(sm, twt, src, dst);
+}
+
+template <int L, int E, int NSIG>
+__global__ void __launch_bounds__(NSIG * L / E) k_col_inv_p2(const float2* __restrict__ X, float2* __restrict__ half,
+                                                             const float2* __restrict__ twt, int n) {
+  extern __shared__ float2 sm[];
+  const int c0 = blockIdx.x * NSIG;
+  ColInvSrc src{X, L, c0};
+  ColCropDst dst{half, n, L, c0};
+  fft_p2<L, E, NSIG, true, false, true>(sm, twt, src, dst);
+}
+
+// Register cap: two CTAs per SM for the CG and plain epilogues; the SDMM
+// epilogue (five operands per pixel) keeps its registers.
+constexpr int p2_rinv_minb(int T, int MODE) { return MODE == kRowOutSdmm ? 1 : (1024 / T > 1 ? 1024 / T : 1); }
+
+template <int L, int E, int NSIG, int MODE>
+__global__ void __launch_bounds__(NSIG * L / E, p2_rinv_minb(NSIG * L / E, MODE)) k_row_inv_p2(const float2* __restrict__ half, RowOutArgs a,
+                                                             const float* __restrict__ dz,
+                                                             const float* __restrict__ beam,
+                                                             const float2* __restrict__ twt, int n,
+                                                             double* partials) {
+  extern __shared__ float2 sm[];
+  const int r0 = blockIdx.x * NSIG;
+  RowInvSrc src{half, L, r0};
+  RowInvDst<MODE> dst;
+  dst.a = a;
+  dst.dz = dz;
+  dst.beam = beam;
+  dst.n = n;
+  dst.L = L;
+  dst.r0 = r0;
+  dst.invL = 1.0f / (float)L;
+  fft_p2<L, E, NSIG, false, false, true>(sm, twt, src, dst);
+  if (MODE == kRowOutCgQ) {
+    double acc[2] = {dst.part[0].value(), dst.part[1].value()};
+    block_reduce<2>(acc);
+    if (threadIdx.x == 0) {
+      partials[kCntDot * 2 * kMaxPartials + blockIdx.x] = acc[0];
+      partials[kCntDot * 2 * kMaxPartials + kMaxPartials + blockIdx.x] = acc[1];
+    }
+  }
+}
+
+// Whether the grid side has the compile-time engine.
+static bool p2_side(int L) { return L == 256 || L == 512 || L == 1024 || L == 2048 || L == 4096; }
+
+// Concatenated twiddle tables of the engine for (L, E) (device, owned by the context).
+template <int L, int E>
+static int p2_table(purify_ctx* c, const float2** out) {
+  const int idx = (E == 16) ? 1 : 0;
+  if (!c->d_twp[idx]) {
+    std::vector<float2> t(std::max(1, p2_twsize(L, E)));
+    p2_twiddles<L, E>(t.data());
+    float2* d = nullptr;
+    if (cudaMalloc((void**)&d, t.size() * sizeof(float2)) != cudaSuccess) return PURIFY_E_ALLOC;
+    if (cudaMemcpy(d, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d);
+      return PURIFY_E_CUDA;
+    }
+    c->d_twp[idx] = d;
+  }
+  *out = c->d_twp[idx];
+  return PURIFY_OK;
+}
+
+template <int L>
+static int p2_prepare_L(purify_ctx* c) {
+  const float2* t;
+  if (int rc = p2_table<L, P2Cfg<L>::E>(c, &t)) return rc;
+  return p2_table<L, P2Cfg<L>::E_CG>(c, &t);
+}
+
+// Twiddle tables of the power-of-two engine, built when the context is
+// created (never inside a stream capture).
+int fft_prepare(purify_ctx* c) {
+  if (c->fft_engine != 1) return PURIFY_OK;
+  switch (c->L) {
+    case 256: return p2_prepare_L<256>(c);
+    case 512: return p2_prepare_L<512>(c);
+    case 1024: return p2_prepare_L<1024>(c);
+    case 2048: return p2_prepare_L<2048>(c);
+    case 4096: return p2_prepare_L<4096>(c);
+    default: c->fft_engine = 0; return PURIFY_OK;
+  }
+}
+
+template <int L>
+static int p2_forward(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j,
+                      const float* beam) {
+  using C = P2Cfg<L>;
+  const float2 *tw, *twcg;
+  if (int rc = p2_table<L, C::E>(c, &tw)) return rc;
+  if (int rc = p2_table<L, C::E_CG>(c, &twcg)) return rc;
+  const double* cgpart = c->d_partials + kCntDot * 2 * kMaxPartials;
+  const int cg_nblk = cg_consumer_blocks(c);
+  const int n = c->n;
+  if (mode == kRowInPlain) {
+    constexpr int NS = C::NS_ROW;
+    constexpr size_t sm = p2_smem_bytes<L, NS>();
+    allow_smem(k_row_fwd_p2<L, C::E, NS, kRowInPlain>, sm);
+    PURIFY_LAUNCH(c, "row_fwd", s,
+                  (k_row_fwd_p2<L, C::E, NS, kRowInPlain><<<n / NS, NS * L / C::E, sm, s>>>(
+                      a, c->d_half, c->d_deapod, beam, tw, n, c->d_sc, cgpart, cg_nblk, cg_j)));
+  } else {
+    constexpr int NS = C::NS_ROWCG;
+    constexpr size_t sm = p2_smem_bytes<L, NS>();
+#define ROWCG(MD)                                                                                         \
+  do {                                                                                                    \
+    allow_smem(k_row_fwd_p2<L, C::E_CG, NS, MD>, sm);                                                     \
+    PURIFY_LAUNCH(c, "row_fwd", s,                                                                        \
+                  (k_row_fwd_p2<L, C::E_CG, NS, MD><<<n / NS, NS * L / C::E_CG, sm, s>>>(                  \
+                      a, c->d_half, c->d_deapod, beam, twcg, n, c->d_sc, cgpart, cg_nblk, cg_j)));          \
+  } while (0)
+    if (mode == kRowInCgUpd) ROWCG(kRowInCgUpd);
+    else ROWCG(kRowInCgFinish);
+#undef ROWCG
+  }
+  {
+    constexpr int NS = C::NS_COL;
+    constexpr size_t sm = p2_smem_bytes<L, NS>();
+    allow_smem(k_col_fwd_p2<L, C::E, NS>, sm);
+    PURIFY_LAUNCH(c, "col_fwd", s,
+                  (k_col_fwd_p2<L, C::E, NS><<<L / NS, NS * L / C::E, sm, s>>>(c->d_half, c->d_grid, tw, n)));
+  }
+  return check_cuda(cudaGetLastError());
+}
+
+template <int L>
+static int p2_adjoint(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaStream_t s, const float2* Xg,
+                      cudaEvent_t before_rows, const float* beam) {
+  using C = P2Cfg<L>;
+  const float2* tw;
+  if (int rc = p2_table<L, C::E>(c, &tw)) return rc;
+  const int n = c->n;
+  {
+    constexpr int NS = C::NS_COL;
+    constexpr size_t sm = p2_smem_bytes<L, NS>();
+    allow_smem(k_col_inv_p2<L, C::E, NS>, sm);
+    PURIFY_LAUNCH(c, "col_inv", s, (k_col_inv_p2<L, C::E, NS><<<L / NS, NS * L / C::E, sm, s>>>(Xg, c->d_half, tw, n)));
+  }
+  if (before_rows) {
+    const int rc = check_cuda(cudaStreamWaitEvent(s, before_rows, 0));
+    if (rc != PURIFY_OK) return rc;
+  }
+  constexpr int NS = C::NS_RINV;
+  constexpr size_t sm = p2_smem_bytes<L, NS>();
+#define ROWI2(MD)                                                                                          \
+  do {                                                                                                     \
+    allow_smem(k_row_inv_p2<L, C::E, NS, MD>, sm);                                                         \
+    PURIFY_LAUNCH(c, "row_inv", s,                                                                         \
+                  (k_row_inv_p2<L, C::E, NS, MD><<<n / NS, NS * L / C::E, sm, s>>>(c->d_half, a, c->d_deapod, \
+                                                                                     beam, tw, n,            \
+                                                                                     c->d_partials)));       \
+  } while (0)
+  if (mode == kRowOutPlain) ROWI2(kRowOutPlain);
+  else if (mode == kRowOutCgQ) ROWI2(kRowOutCgQ);
+  else ROWI2(kRowOutSdmm);
+#undef ROWI2
+  return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 // Blocks of the inverse row pass, i.e. the CG inner-product partials it leaves.
-int cg_partial_blocks(const purify_ctx* c) { return c->n / row_shape(c).nsig; }
+int cg_partial_blocks(const purify_ctx* c) {
+  switch (p2_side(c->L) ? c->L : 0) {
+    case 256: return c->n / P2Cfg<256>::NS_RINV;
+    case 512: return c->n / P2Cfg<512>::NS_RINV;
+    case 1024: return c->n / P2Cfg<1024>::NS_RINV;
+    case 2048: return c->n / P2Cfg<2048>::NS_RINV;
+    case 4096: return c->n / P2Cfg<4096>::NS_RINV;
+    default: return c->n / row_shape(c).nsig;
+  }
+}
 
 int cg_consumer_blocks(const purify_ctx* c) {
   const int nb = cg_partial_blocks(c);
@@ -380,6 +609,16 @@ int launch_cg_scalars(purify_ctx* c, int cg_j, cudaStream_t s) {
 
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j) {
   const float* beam = c->beam_on ? c->d_beam : nullptr;
+  if (c->fft_engine == 1) {
+    switch (c->L) {
+      case 256: return p2_forward<256>(c, mode, a, s, cg_j, beam);
+      case 512: return p2_forward<512>(c, mode, a, s, cg_j, beam);
+      case 1024: return p2_forward<1024>(c, mode, a, s, cg_j, beam);
+      case 2048: return p2_forward<2048>(c, mode, a, s, cg_j, beam);
+      case 4096: return p2_forward<4096>(c, mode, a, s, cg_j, beam);
+      default: break;
+    }
+  }
   const FftShape rs = row_shape(c), cs = col_shape(c);
   const double* cgpart = c->d_partials + kCntDot * 2 * kMaxPartials;
   const int cg_nblk = cg_consumer_blocks(c);
@@ -424,6 +663,16 @@ int phi_adjoint_image(purify_ctx* c, RowOutMode mode, const RowOutArgs& a, cudaS
                       cudaEvent_t before_rows) {
   const float* beam = c->beam_on ? c->d_beam : nullptr;
   const float2* Xg = grid ? grid : c->d_grid;
+  if (c->fft_engine == 1) {
+    switch (c->L) {
+      case 256: return p2_adjoint<256>(c, mode, a, s, Xg, before_rows, beam);
+      case 512: return p2_adjoint<512>(c, mode, a, s, Xg, before_rows, beam);
+      case 1024: return p2_adjoint<1024>(c, mode, a, s, Xg, before_rows, beam);
+      case 2048: return p2_adjoint<2048>(c, mode, a, s, Xg, before_rows, beam);
+      case 4096: return p2_adjoint<4096>(c, mode, a, s, Xg, before_rows, beam);
+      default: break;
+    }
+  }
   const FftShape rs = row_shape(c), cs = col_shape(c);
   const size_t smr = (size_t)(rs.nsig + 1) * c->L * sizeof(float2);
   const size_t smc = (size_t)(cs.nsig + 1) * c->L * sizeof(float2);

@@ -20,7 +20,6 @@
 namespace purify {
 
 constexpr int kTile = 16;     // coefficient tile (analysis) / half output tile (synthesis)
-constexpr int kMaxTaps = 16;  // db8
 
 struct LevelGeom {
   int tile;     // coefficient tile side (analysis) / half output tile (synthesis); divides L/2
@@ -37,15 +36,6 @@ struct LevelGeom {
 struct BasisList {
   int p[8];     // Daubechies order of wavelet plane k
 };
-
-__device__ __forceinline__ void load_filters(const WaveletFilters& wf, int p, float* h, float* g) {
-  const int len = 2 * p;
-  for (int m = threadIdx.x; m < len; m += blockDim.x) {
-    h[m] = wf.h[wf.off[p] + m];
-    const float hr = wf.h[wf.off[p] + len - 1 - m];
-    g[m] = (m & 1) ? -hr : hr;
-  }
-}
 
 // Soft threshold + dual update for one final coefficient alpha at index j;
 // returns w |alpha| (its term of f1), summed per thread in FP32 (a few terms)
@@ -98,75 +88,78 @@ __global__ void k_dirac(const float2* __restrict__ x, float2* __restrict__ alpha
   }
 }
 
-// ---------------------------------------------------------------------------
-// One analysis level for every wavelet plane.
-//   input  : level 0: x (shared by all planes); else ll_in + k * (n/2)^2, L x L
-//   output : LH, HL, HH at their Mallat positions of plane k; LL to
-//            ll_out + k * (n/2)^2, or to the plane on the last level.
-// CTA: coefficient tile [I1, I1 + TI) x [I2, I2 + TI) of the L/2 x L/2 sub-bands.
-// ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in, int in_shared,
-                                                   float2* __restrict__ ll_out, float2* __restrict__ coef,
-                                                   LevelGeom G, BasisList bl, WaveletFilters wf,
-                                                   SaraProxArgs pa, double* partials, DevScalars* sc) {
-  __shared__ float h[kMaxTaps], g[kMaxTaps];
+// One wavelet plane of one analysis level, for the Daubechies order P fixed at
+// compile time (filters in registers, tap loops unrolled).  Returns this
+// thread's terms of f1 (prox mode).
+template <int P, int MODE>
+__device__ __forceinline__ float dwt_plane(const float2* __restrict__ in, int in_shared, float2* __restrict__ ll_out,
+                                           float2* __restrict__ coef, const LevelGeom& G, const WaveletFilters& wf,
+                                           const SaraProxArgs& pa, int k, float gamma) {
   extern __shared__ float2 sm[];
-  const int k = blockIdx.z;
-  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
+  constexpr int taps = 2 * P;
+  constexpr int hoff = P * (P - 1);  // db_p starts after db_1 .. db_(p-1): sum of 2q, q < p
+  float h[taps], g[taps];
+#pragma unroll
+  for (int m = 0; m < taps; ++m) {
+    h[m] = wf.h[hoff + m];
+    const float hr = wf.h[hoff + taps - 1 - m];
+    g[m] = (m & 1) ? -hr : hr;
+  }
   float f1 = 0.f;
-  if (k == G.nb) {
-    // the Dirac plane (first level only): alpha_0 = x / sqrt(q) on this CTA's
-    // 2TI x 2TI block of pixels, with its prox update
-    const int TI = G.tile, r0 = 2 * blockIdx.y * TI, c0 = 2 * blockIdx.x * TI;
-    const size_t base = (size_t)G.dirac * G.n * G.n;
-    for (int e = threadIdx.x; e < 4 * TI * TI; e += blockDim.x) {
-      const int rr = e / (2 * TI), cc = e - rr * (2 * TI);
-      const size_t j = (size_t)(r0 + rr) * G.n + c0 + cc;
-      const float2 al = cscale(in[j], G.scale);
-      if (MODE == kSaraPlain) coef[base + j] = al;
-      else f1 += sara_prox(al, base + j, pa, gamma);
-    }
-  } else {
-  const int p = bl.p[k];
-  const int taps = 2 * p;
   const int L = G.L, H = L / 2;
   const int TI = G.tile;
   const int I1 = blockIdx.y * TI, I2 = blockIdx.x * TI;
   const int RH = 2 * TI + taps - 2;  // input rows/cols the tile needs
   float2* inb = sm;                  // RH x RH
   float2* rowp = sm + RH * RH;       // RH x 2TI  ([a | d] per input row)
-  load_filters(wf, p, h, g);
   const float2* src = in_shared ? in : in + (size_t)k * (G.n / 2) * (G.n / 2);
-  const Div dL = make_div(L), dTI = make_div(TI), d2TI = make_div(2 * TI);
-  // input tile with its halo (periodic): eight loads per thread in flight per round
-  for (int k0 = 0; k0 < RH * RH; k0 += 8 * (int)blockDim.x) {
-    float2 v[8];
+  const Div dTI = make_div(TI), d2TI = make_div(2 * TI);
+  // input tile with its halo (periodic): warps take rows, lanes columns (RH <=
+  // 2 * 16 + 14 = 46, two column rounds); the halo wraps past L at most once
+  // when L >= RH, and index by index (a remainder) otherwise
+  {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rr0 = (threadIdx.x >> 5); rr0 < RH; rr0 += 4 * nw) {
+      float2 v[4][2];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = k0 + threadIdx.x + q * blockDim.x;
-      if (e < RH * RH) {
-        const int rr = e / RH, cc = e - rr * RH;
-        int r = 2 * I1 + rr, c = 2 * I2 + cc;
-        r -= udiv(r, dL) * L;
-        c -= udiv(c, dL) * L;
-        v[q] = src[(size_t)r * L + c];
+      for (int q = 0; q < 4; ++q) {
+        const int rr = rr0 + q * nw;
+        if (rr < RH) {
+          int r = 2 * I1 + rr;
+          r = (L >= RH) ? (r >= L ? r - L : r) : r % L;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cc = lane + 32 * h;
+            if (cc < RH) {
+              int c = 2 * I2 + cc;
+              c = (L >= RH) ? (c >= L ? c - L : c) : c % L;
+              v[q][h] = src[(size_t)r * L + c];
+            }
+          }
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = k0 + threadIdx.x + q * blockDim.x;
-      if (e < RH * RH) inb[e] = v[q];
+      for (int q = 0; q < 4; ++q) {
+        const int rr = rr0 + q * nw;
+        if (rr < RH) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cc = lane + 32 * h;
+            if (cc < RH) inb[rr * RH + cc] = v[q][h];
+          }
+        }
+      }
     }
   }
   __syncthreads();
   // rows: a[i2] = sum_m h[m] s[2 i2 + m], d[i2] = sum_m g[m] s[2 i2 + m]
   for (int idx = threadIdx.x; idx < RH * TI; idx += blockDim.x) {
     const int rr = udiv(idx, dTI), i2 = idx - rr * TI;
-    const float2* s = inb + rr * RH + 2 * i2;
+    const float2* sp = inb + rr * RH + 2 * i2;
     float2 a = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+#pragma unroll
     for (int m = 0; m < taps; ++m) {
-      const float2 v = s[m];
+      const float2 v = sp[m];
       a.x = fmaf(h[m], v.x, a.x); a.y = fmaf(h[m], v.y, a.y);
       d.x = fmaf(g[m], v.x, d.x); d.y = fmaf(g[m], v.y, d.y);
     }
@@ -189,8 +182,10 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
     float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
     if (idxv[t] >= 0) {
       const int i1 = udiv(idx, d2TI), kc = idx - i1 * (2 * TI);
+      const float2* cp = rowp + (2 * i1) * (2 * TI) + kc;
+#pragma unroll
       for (int m = 0; m < taps; ++m) {
-        const float2 v = rowp[(2 * i1 + m) * (2 * TI) + kc];
+        const float2 v = cp[m * (2 * TI)];
         lo.x = fmaf(h[m], v.x, lo.x); lo.y = fmaf(h[m], v.y, lo.y);
         hi.x = fmaf(g[m], v.x, hi.x); hi.y = fmaf(g[m], v.y, hi.y);
       }
@@ -251,6 +246,48 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
     for (int o = 0; o < 2 * kMaxIdx; ++o)
       if (to_plane[o]) f1 += sara_prox_v(ao[o], zv[o], wv[o], pbase + jo[o], pa, gamma);
   }
+    return f1;
+}
+
+// ---------------------------------------------------------------------------
+// One analysis level for every wavelet plane.
+//   input  : level 0: x (shared by all planes); else ll_in + k * (n/2)^2, L x L
+//   output : LH, HL, HH at their Mallat positions of plane k; LL to
+//            ll_out + k * (n/2)^2, or to the plane on the last level.
+// CTA: coefficient tile [I1, I1 + TI) x [I2, I2 + TI) of the L/2 x L/2 sub-bands.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in, int in_shared,
+                                                   float2* __restrict__ ll_out, float2* __restrict__ coef,
+                                                   LevelGeom G, BasisList bl, WaveletFilters wf,
+                                                   SaraProxArgs pa, double* partials, DevScalars* sc) {
+  extern __shared__ float2 sm[];
+  const int k = blockIdx.z;
+  const float gamma = (MODE == kSaraProx) ? (float)sc->gamma : 0.f;
+  float f1 = 0.f;
+  if (k == G.nb) {
+    // the Dirac plane (first level only): alpha_0 = x / sqrt(q) on this CTA's
+    // 2TI x 2TI block of pixels, with its prox update
+    const int TI = G.tile, r0 = 2 * blockIdx.y * TI, c0 = 2 * blockIdx.x * TI;
+    const size_t base = (size_t)G.dirac * G.n * G.n;
+    for (int e = threadIdx.x; e < 4 * TI * TI; e += blockDim.x) {
+      const int rr = e / (2 * TI), cc = e - rr * (2 * TI);
+      const size_t j = (size_t)(r0 + rr) * G.n + c0 + cc;
+      const float2 al = cscale(in[j], G.scale);
+      if (MODE == kSaraPlain) coef[base + j] = al;
+      else f1 += sara_prox(al, base + j, pa, gamma);
+    }
+  } else {
+    switch (bl.p[k]) {
+      case 1: f1 += dwt_plane<1, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 2: f1 += dwt_plane<2, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 3: f1 += dwt_plane<3, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 4: f1 += dwt_plane<4, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 5: f1 += dwt_plane<5, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 6: f1 += dwt_plane<6, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      case 7: f1 += dwt_plane<7, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+      default: f1 += dwt_plane<8, MODE>(in, in_shared, ll_out, coef, G, wf, pa, k, gamma); break;
+    }
   }
   if (MODE == kSaraProx) {
     double f1d = (double)f1, tot;
@@ -262,6 +299,79 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
         sc->zeta = (prev != 0.0) ? fabs(sc->f1 - prev) / fabs(prev) : INFINITY;
         sc->f1_prev = sc->f1;
       }
+    }
+  }
+}
+
+// Column then row synthesis of one plane's coefficient windows (in shared
+// memory) for the Daubechies order P fixed at compile time; the finest level
+// accumulates into accum, coarser levels write their low-low output.
+constexpr int kIdwtMaxOut = 4;  // (2TO)^2 / blockDim outputs per thread: 1024 / 256
+template <int P>
+__device__ __forceinline__ void idwt_filter(const float2* LLs, const float2* HLs, const float2* LHs,
+                                            const float2* HHs, float2* As, float2* Ds, const LevelGeom& G,
+                                            const WaveletFilters& wf, int k, int K1, int K2,
+                                            float2* __restrict__ ll_out, float2 (&accum)[kIdwtMaxOut]) {
+  constexpr int taps = 2 * P;
+  constexpr int hoff = P * (P - 1);
+  float h[taps], g[taps];
+#pragma unroll
+  for (int m = 0; m < taps; ++m) {
+    h[m] = wf.h[hoff + m];
+    const float hr = wf.h[hoff + taps - 1 - m];
+    g[m] = (m & 1) ? -hr : hr;
+  }
+  const int L = G.L;
+  const int TO = G.tile;
+  const int CW = TO + P - 1;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nout = (2 * TO) * (2 * TO);
+  const Div d2TO = make_div(2 * TO);
+  // column synthesis: output row kappa1 in [0, 2TO), window column t2;
+  // taps of one parity: m = par + 2u, t1 = (k1 - par) / 2 - u + P - 1
+  for (int t2 = threadIdx.x >> 5; t2 < CW; t2 += nw)
+    for (int k1 = lane; k1 < 2 * TO; k1 += 32) {
+      const int idx = k1 * CW + t2;
+      const int par = k1 & 1;
+      const int tb = (k1 - par) / 2 + P - 1;
+      float2 av = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int t1 = tb - u;
+        const float hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
+        const float2 ll = LLs[t1 * CW + t2], hl = HLs[t1 * CW + t2];
+        const float2 lh = LHs[t1 * CW + t2], hh = HHs[t1 * CW + t2];
+        av.x = fmaf(hm, ll.x, fmaf(gm, hl.x, av.x));
+        av.y = fmaf(hm, ll.y, fmaf(gm, hl.y, av.y));
+        dv.x = fmaf(hm, lh.x, fmaf(gm, hh.x, dv.x));
+        dv.y = fmaf(hm, lh.y, fmaf(gm, hh.y, dv.y));
+      }
+      As[idx] = av;
+      Ds[idx] = dv;
+    }
+  __syncthreads();
+  // row synthesis
+#pragma unroll
+  for (int t = 0; t < kIdwtMaxOut; ++t) {
+    const int idx = threadIdx.x + t * blockDim.x;
+    if (idx >= nout) continue;
+    const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
+    const int par = k2 & 1;
+    const int tb = (k2 - par) / 2 + P - 1;
+    float2 sacc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int t2 = tb - u;
+      const float hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
+      const float2 av = As[k1 * CW + t2], dv = Ds[k1 * CW + t2];
+      sacc.x = fmaf(hm, av.x, fmaf(gm, dv.x, sacc.x));
+      sacc.y = fmaf(hm, av.y, fmaf(gm, dv.y, sacc.y));
+    }
+    if (G.last) {
+      accum[t] = cadd(accum[t], sacc);
+    } else {
+      const int gk1 = K1 + k1, gk2 = K2 + k2;
+      if (gk1 < L && gk2 < L) ll_out[(size_t)k * (G.n / 2) * (G.n / 2) + (size_t)gk1 * L + gk2] = sacc;
     }
   }
 }
@@ -278,7 +388,6 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
                                                     float2* __restrict__ ll_out, const float2* __restrict__ coef,
                                                     float2* __restrict__ x, int dirac_plane, LevelGeom G,
                                                     BasisList bl, WaveletFilters wf) {
-  __shared__ float h[kMaxTaps], g[kMaxTaps];
   extern __shared__ float2 sm[];
   const int L = G.L, H = L / 2;
   const int TO = G.tile;
@@ -286,11 +395,10 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   // the finest level loops over all planes in one CTA; otherwise one plane per z
   const int kbeg = G.last ? 0 : blockIdx.z;
   const int kend = G.last ? G.nb : blockIdx.z + 1;
-  constexpr int kMaxOut = 4;  // (2TO)^2 / blockDim outputs per thread: 1024 / 256
+  constexpr int kMaxOut = kIdwtMaxOut;
   float2 accum[kMaxOut];
   const int nout = (2 * TO) * (2 * TO);
   const Div dH = make_div(H), d2TO = make_div(2 * TO);
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
   for (int t = 0; t < kMaxOut; ++t) accum[t] = make_float2(0.f, 0.f);
   // the four coefficient windows of plane kk, loaded into registers (CW^2 <=
@@ -305,11 +413,12 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     const int lls = ll_from_plane ? G.n : H;
     // window origin: coefficient K/2 - p + 1 (mod H), shifted to stay >= 0
     const int o1 = K1 / 2 - pk + 1 + 8 * H, o2 = K2 / 2 - pk + 1 + 8 * H;
+    const float rcw = 1.0f / (float)CWk;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < CWk * CWk) {
-        const int t1 = e / CWk, t2 = e - t1 * CWk;
+        const int t1 = quot_small(e, rcw), t2 = e - t1 * CWk;
         int c1 = o1 + t1, c2 = o2 + t2;
         c1 -= udiv(c1, dH) * H;
         c2 -= udiv(c2, dH) * H;
@@ -323,7 +432,6 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   issue(kbeg);
   for (int k = kbeg; k < kend; ++k) {
     const int p = bl.p[k];
-    const int taps = 2 * p;
     const int CW = TO + p - 1;                 // coefficient window per axis
     float2* LLs = sm;                          // CW x CW each
     float2* HLs = LLs + CW * CW;
@@ -332,7 +440,6 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     float2* As = HHs + CW * CW;                // 2TO x CW
     float2* Ds = As + 2 * TO * CW;             // 2TO x CW
     __syncthreads();
-    load_filters(wf, p, h, g);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
@@ -345,43 +452,15 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
     }
     __syncthreads();
     if (k + 1 < kend) issue(k + 1);
-    // column synthesis: output row kappa1 in [0, 2TO), window column t2
-    for (int t2 = threadIdx.x >> 5; t2 < CW; t2 += nw)
-    for (int k1 = lane; k1 < 2 * TO; k1 += 32) {
-      const int idx = k1 * CW + t2;
-      float2 av = make_float2(0.f, 0.f), dv = make_float2(0.f, 0.f);
-      for (int m = (k1 & 1); m < taps; m += 2) {
-        const int t1 = (k1 - m) / 2 + p - 1;  // k1 - m even
-        const float2 ll = LLs[t1 * CW + t2], hl = HLs[t1 * CW + t2];
-        const float2 lh = LHs[t1 * CW + t2], hh = HHs[t1 * CW + t2];
-        av.x = fmaf(h[m], ll.x, fmaf(g[m], hl.x, av.x));
-        av.y = fmaf(h[m], ll.y, fmaf(g[m], hl.y, av.y));
-        dv.x = fmaf(h[m], lh.x, fmaf(g[m], hh.x, dv.x));
-        dv.y = fmaf(h[m], lh.y, fmaf(g[m], hh.y, dv.y));
-      }
-      As[idx] = av;
-      Ds[idx] = dv;
-    }
-    __syncthreads();
-    // row synthesis
-#pragma unroll
-    for (int t = 0; t < kMaxOut; ++t) {
-      const int idx = threadIdx.x + t * blockDim.x;
-      if (idx >= nout) continue;
-      const int k1 = udiv(idx, d2TO), k2 = idx - k1 * (2 * TO);
-      float2 s = make_float2(0.f, 0.f);
-      for (int m = (k2 & 1); m < taps; m += 2) {
-        const int t2 = (k2 - m) / 2 + p - 1;
-        const float2 av = As[k1 * CW + t2], dv = Ds[k1 * CW + t2];
-        s.x = fmaf(h[m], av.x, fmaf(g[m], dv.x, s.x));
-        s.y = fmaf(h[m], av.y, fmaf(g[m], dv.y, s.y));
-      }
-      if (G.last) {
-        accum[t] = cadd(accum[t], s);
-      } else {
-        const int gk1 = K1 + k1, gk2 = K2 + k2;
-        if (gk1 < L && gk2 < L) ll_out[(size_t)k * (G.n / 2) * (G.n / 2) + (size_t)gk1 * L + gk2] = s;
-      }
+    switch (p) {
+      case 1: idwt_filter<1>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 2: idwt_filter<2>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 3: idwt_filter<3>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 4: idwt_filter<4>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 5: idwt_filter<5>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 6: idwt_filter<6>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      case 7: idwt_filter<7>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
+      default: idwt_filter<8>(LLs, HLs, LHs, HHs, As, Ds, G, wf, k, K1, K2, ll_out, accum); break;
     }
   }
   if (G.last) {

@@ -167,3 +167,19 @@ def test_tile_schedules_agree(n, M, J, tmp_path):
     entry = autotune.autotune_tile(n, uv, J, cache_path=cache, reps=3)
     assert entry["tile"] in autotune.valid_tiles(n, J)
     assert autotune.autotune_tile(n, uv, J, cache_path=cache)["tile"] == entry["tile"]
+
+
+# Power-of-two grids of the compile-time FFT engine (2n = 256 .. 4096), each
+# against the oracle: both zero-padding prunings, every row and column pass.
+@pytest.mark.parametrize("n,M,J", [(128, 4000, 4), (512, 20000, 6), (2048, 20000, 6)])
+def test_phi_and_adjoint_power_of_two_grids(n, M, J):
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(n + 7)
+    uv = inputs.uv_variable_density(M, n, rng).astype(np.float32).astype(np.float64)
+    x = inputs.random_image(n, rng)
+    v = inputs.random_vis(M, rng)
+    ctx = binding.Context(n, uv.astype(np.float32), J=J, levels=4)
+    assert rel_err(host(ctx.phi(dev(x, torch))), me.phi(x, uv, J)) <= TOL
+    assert rel_err(host(ctx.phi_adj(dev(v, torch))), me.phi_adj(v, uv, n, J)) <= TOL

@@ -1,7 +1,7 @@
 """Host checks of index arithmetic used by the CUDA kernels.
 
 The gridding kernel divides small non-negative integers by the halo and key
-widths with a rounded float reciprocal (`quot_small` in `csrc/gridding.cu`):
+widths with a rounded float reciprocal (`quot_small` in `csrc/common.cuh`):
 floor(k / d) = trunc(rn(rn(k + 1/2) * rn(1/d))).  IEEE float32 arithmetic
 with round-to-nearest is the same on the host (numpy) and the device
 (`__fadd_rn`, `__fmul_rn`, correctly rounded division), so the identity is
