@@ -395,6 +395,75 @@ int purify_batch_size(const purify_batch* batch, int32_t* count,
                       int32_t* kernels_per_iteration);
 void purify_batch_destroy(purify_batch* batch);
 
+/* ------------------------------------------------------------------------
+ * Differentiation of the SDMM iteration (reverse mode, hand-written).
+ *
+ * One iteration of Algorithm 1 (§4.3-§4.4 with S = 3) for the weighted
+ * problem min ||W Psi^H x||_1 s.t. ||y_w - Phi_w x||_2 <= eps, x >= 0, where
+ * Phi_w = diag(w) Phi and y_w = w o y fold per-visibility weights into the
+ * measurement operator (§5 notes weighting matrices fold into Phi), run
+ * forward with a tape and reversed from it:
+ *   step 5  x_hat' = k steps of standard CG on Q_w = Phi_w^H Phi_w + 2I from
+ *           x0 = x_hat with b = x1 + x2 + x3 (stopping early if <r, r> = 0);
+ *   i = 1   a1 = Psi^H x_hat' + z1, r1 = prox1(a1) (eq. prox1, lam = gamma w_j),
+ *           z1' = a1 - r1, x1' = Psi (2 r1 - a1);
+ *   i = 2   a2 = Phi_w x_hat' + z2, r2 = projection of a2 onto the ball of
+ *           radius eps around y_w (eq. prox2, reading c1), z2' = a2 - r2,
+ *           x2' = Phi_w^H (2 r2 - a2);
+ *   i = 3   a3 = x_hat' + z3, r3 = max(Re a3, 0) (eq. prox3), z3' = a3 - r3,
+ *           x3' = 2 r3 - a3.
+ * The state is seven DEVICE complex64 arrays in this order: x_hat (N),
+ * z1 (D), z2 (M), z3 (N), x1 (N), x2 (N), x3 (N); visibility-indexed arrays
+ * (y, w, z2) are in the caller's order of the context's uv.  omega (D
+ * float32) are the weights of f1, w (M float32) the visibility weights.
+ * Complex entries are treated as real pairs (§4.1): the adjoint of an entry
+ * is dL/dRe + i dL/dIm.  The calls synchronise `stream` (the CG step sizes
+ * are formed on the host in FP64).  cg_iters is 0..64. */
+
+/* gamma = beta ||Psi^H Phi_w^H y_w||_inf (§4.4's rule for the weighted
+ * problem) into *gamma (host).  y, wvis: M entries (device, caller order). */
+int purify_diff_penalty(purify_ctx* ctx, const float* y, const float* wvis, double beta, double* gamma,
+                        purify_stream_t stream);
+
+/* Bytes of the device tape of one iteration with cg_iters CG steps. */
+int purify_diff_tape_bytes(purify_ctx* ctx, int32_t cg_iters, size_t* bytes);
+
+/* Forward: state_out = one iteration of state_in (arrays may not alias), the
+ * intermediate vectors and CG step sizes written to `tape` (device memory of
+ * purify_diff_tape_bytes bytes, owned by the caller). */
+int purify_diff_iteration(purify_ctx* ctx, const float* y, const float* wvis, const float* omega,
+                          double gamma, double eps, int32_t cg_iters, const float* const* state_in,
+                          float* const* state_out, void* tape, purify_stream_t stream);
+
+/* Vector-Jacobian product of that iteration: given the adjoints of its
+ * outputs (bar_out, seven arrays like the state) and the state_in and tape
+ * of its forward, writes the adjoints of its inputs to bar_in (seven arrays,
+ * distinct from bar_out) and ADDS the weights' adjoints to wvis_bar (M
+ * float32) and omega_bar (D float32).  gamma is held constant. */
+int purify_diff_iteration_vjp(purify_ctx* ctx, const float* y, const float* wvis, const float* omega,
+                              double gamma, double eps, int32_t cg_iters, const float* const* state_in,
+                              const void* tape, float* const* bar_out, float* const* bar_in,
+                              float* wvis_bar, float* omega_bar, purify_stream_t stream);
+
+/* VJP of the weighted soft threshold of §4.4 eq. prox1, r = a/|a| (|a| - gamma
+ * w)^+: abar = J^T rbar, (1 - lam/|a|) rbar + lam/|a|^3 a <a, rbar> where
+ * |a| > lam = gamma w, else 0; when wbar is not NULL, wbar += gamma dL/dlam
+ * with dL/dlam = -<a, rbar>/|a| (0 where |a| <= lam).  count complex entries;
+ * w NULL means w = 1.  All device pointers. */
+int purify_vjp_soft_threshold(int64_t count, const float* a, const float* w, float gamma, const float* rbar,
+                              float* abar, float* wbar, purify_stream_t stream);
+
+/* VJP of the projection onto the ball ||r - y|| <= eps (§4.3 B, eq. prox2 read
+ * as that projection): inside abar = rbar; outside, with d = a - y and c =
+ * eps/||d||, abar = c (rbar - d <d, rbar>/||d||^2), and ybar = rbar - abar
+ * when ybar is not NULL.  FP64 norms.  Synchronises `stream`. */
+int purify_vjp_l2ball(purify_ctx* ctx, int64_t count, const float* a, const float* y, double eps,
+                      const float* rbar, float* abar, float* ybar, purify_stream_t stream);
+
+/* VJP of the positivity projection of §4.4 eq. prox3, r = max(Re a, 0) + 0i:
+ * abar = (Re rbar where Re a > 0, else 0) + 0i. */
+int purify_vjp_positive(int64_t count, const float* a, const float* rbar, float* abar, purify_stream_t stream);
+
 /* Kernel timing (measurement utility; the paper has no counterpart).
  * purify_profile_enable(ctx, 1) makes every later kernel launch of this
  * context record a CUDA event before and after it on its stream;

@@ -10,16 +10,21 @@
   min ||W Psi^H x||_1 s.t. ||y_w - Phi_w x||_2 <= eps, x >= 0, with
   per-visibility weights w (Phi_w = diag(w) Phi, y_w = diag(w) y; the
   weighting matrices §5 says fold into the measurement operator) and SARA
-  weights omega.  The forward keeps the SDMM state every ``checkpoint``
-  iterations; the backward recomputes one segment at a time from its
-  checkpoint and back-propagates through it, so memory holds one segment's
-  graph, not K iterations'.  The x-update is the conjugate-gradient method
-  truncated at k steps and is differentiated exactly as run (including its
-  data-dependent step sizes), not through the implicit-function shortcut.
-  gamma is a constant of the forward (held fixed for the derivative).
+  weights omega.  Each iteration is the library's purify_diff_iteration
+  (CUDA kernels; the CG step sizes in FP64 on the host) and its backward
+  the library's purify_diff_iteration_vjp: CG reversed from the step sizes
+  and vectors on the tape, and the Jacobians of the soft threshold, the
+  l2-ball projection and the positivity projection.  The forward keeps the
+  SDMM state every ``checkpoint`` iterations; the backward re-runs one
+  segment at a time from its checkpoint (with tapes) and reverses it, so
+  memory holds one segment's tapes, not K iterations'.  The x-update is
+  the conjugate-gradient method truncated at k steps and is differentiated
+  exactly as run (including its data-dependent step sizes), not through the
+  implicit-function shortcut.  gamma is a constant of the forward (held
+  fixed for the derivative).
 
-The linear operators run in the CUDA library; the entrywise parts (prox,
-projections, CG vector updates) are torch operations.
+Every arithmetic step runs in the CUDA library; torch holds the tensors and
+the autograd graph.
 """
 from __future__ import annotations
 
@@ -74,140 +79,91 @@ class PsiFn(torch.autograd.Function):
         return ctx.op.sara_analysis(gx.contiguous().reshape(-1)).clone(), None
 
 
-def _cdot(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
-    """Re <a, b> accumulated in FP64."""
-    return (a.real.double() * b.real.double() + a.imag.double() * b.imag.double()).sum()
+def initial_state(op: binding.Context) -> list:
+    """Algorithm 1 steps 1-3 with x_hat(0) = 0: every state array zero."""
+    return [torch.zeros(n, dtype=torch.complex64, device=op.device) for n in op.diff_state_shapes()]
 
 
-def _soft(a: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
-    """a / |a| (|a| - lam)^+ with a derivative that stays finite at a = 0."""
-    mag = torch.sqrt(a.real * a.real + a.imag * a.imag + 1e-30)
-    return a * (torch.relu(mag - lam) / mag)
+def penalty(op: binding.Context, y: torch.Tensor, wv: torch.Tensor, beta: float = 1e-3) -> float:
+    """gamma = beta ||Psi^H Phi_w^H y_w||_inf (§4.4), on the device."""
+    return op.diff_penalty(y.contiguous(), wv.detach().contiguous(), beta)
 
 
 class _Problem:
     """Operators and data of one weighted problem."""
 
     def __init__(self, op: binding.Context, y: torch.Tensor, eps: float, gamma: float, cg_iters: int):
-        self.op, self.y, self.eps, self.gamma, self.cg_iters = op, y, float(eps), float(gamma), int(cg_iters)
+        self.op, self.y, self.eps, self.gamma, self.cg_iters = op, y.contiguous(), float(eps), float(gamma), int(cg_iters)
 
-    def phi_w(self, x, wv):
-        return wv * PhiFn.apply(x, self.op)
+    def step(self, state, wv, omega, tape):
+        """One iteration of Algorithm 1 (purify_diff_iteration), its tape filled."""
+        out = [torch.empty_like(t) for t in state]
+        self.op.diff_iteration(self.y, wv, omega, self.gamma, self.eps, self.cg_iters, state, out, tape)
+        return out
 
-    def phi_w_adj(self, v, wv):
-        return PhiAdjFn.apply(wv * v, self.op)
-
-    def iterate(self, state, wv, omega):
-        """One pass of Algorithm 1 steps 5-9 (torch, differentiable)."""
-        x_hat, z1, z2, z3, x1, x2, x3 = state
-        op = self.op
-
-        def apply_q(v):
-            return self.phi_w_adj(self.phi_w(v, wv), wv) + 2.0 * v
-
-        # step 5: CG from the previous x_hat, k steps (standard CG, FP64 inner products)
-        b = x1 + x2 + x3
-        x = x_hat
-        r = b - apply_q(x)
-        p = r
-        rho = _cdot(r, r)
-        for _ in range(self.cg_iters):
-            q = apply_q(p)
-            pq = _cdot(p, q)
-            alpha = torch.where(pq > 0, rho / torch.where(pq > 0, pq, torch.ones_like(pq)), torch.zeros_like(pq))
-            x = x + alpha.to(torch.float32) * p
-            r = r - alpha.to(torch.float32) * q
-            rho_new = _cdot(r, r)
-            beta = torch.where(rho > 0, rho_new / torch.where(rho > 0, rho, torch.ones_like(rho)), torch.zeros_like(rho))
-            p = r + beta.to(torch.float32) * p
-            rho = rho_new
-        x_hat = x
-        # i = 1: weighted soft threshold on Psi^H x_hat
-        s1 = PsiAdjFn.apply(x_hat, op).reshape(z1.shape)
-        a1 = s1 + z1
-        r1 = _soft(a1, self.gamma * omega)
-        z1 = a1 - r1
-        x1 = PsiFn.apply(r1 - z1, op)
-        # i = 2: projection onto the l2 ball around y_w
-        yw = wv * self.y
-        s2 = self.phi_w(x_hat, wv)
-        a2 = s2 + z2
-        d = a2 - yw
-        nd = torch.sqrt(_cdot(d, d))
-        scale = torch.clamp(self.eps / nd, max=1.0).to(torch.float32)
-        r2 = yw + scale * d
-        z2 = a2 - r2
-        x2 = self.phi_w_adj(r2 - z2, wv)
-        # i = 3: positive orthant
-        a3 = x_hat + z3
-        r3 = torch.complex(torch.relu(a3.real), torch.zeros_like(a3.real))
-        z3 = a3 - r3
-        x3 = r3 - z3
-        return (x_hat, z1, z2, z3, x1, x2, x3)
-
-
-def initial_state(op: binding.Context) -> tuple:
-    dev = op.device
-    zi = torch.zeros((op.n, op.n), dtype=torch.complex64, device=dev)
-    return (zi, torch.zeros((op.q, op.n, op.n), dtype=torch.complex64, device=dev),
-            torch.zeros(op.M, dtype=torch.complex64, device=dev), zi.clone(), zi.clone(), zi.clone(), zi.clone())
-
-
-def penalty(op: binding.Context, y: torch.Tensor, wv: torch.Tensor, beta: float = 1e-3) -> float:
-    """gamma = beta ||Psi^H Phi_w^H y_w||_inf (§4.4)."""
-    with torch.no_grad():
-        d = op.phi_adj((wv * wv * y).contiguous())
-        return float(beta * op.sara_analysis(d.reshape(-1)).abs().max().item())
+    def step_vjp(self, state, tape, bar_out, wv, omega, w_bar, om_bar):
+        """Adjoints of one iteration's inputs (purify_diff_iteration_vjp); adds to w_bar, om_bar."""
+        bar_in = [torch.empty_like(t) for t in state]
+        self.op.diff_iteration_vjp(self.y, wv, omega, self.gamma, self.eps, self.cg_iters, state, tape, bar_out,
+                                   bar_in, w_bar, om_bar)
+        return bar_in
 
 
 class SDMMUnrolled(torch.autograd.Function):
-    """x_K of K SDMM iterations as a function of (w, omega), with checkpointing."""
+    """x_K of K SDMM iterations as a function of (w, omega), with checkpointing.
+
+    Forward: K calls of the library's differentiable iteration, keeping the
+    state every ``checkpoint`` iterations.  Backward: per segment (last
+    first), the iterations are re-run from the segment's checkpoint with
+    their tapes kept, then reversed one by one with the hand-written
+    vector-Jacobian product of the library (CG reversed from its stored step
+    sizes and vectors, the Jacobians of the three proximity operators).
+    Memory holds one segment's states and tapes, not K iterations'."""
 
     @staticmethod
     def forward(ctx, wv, omega, problem: _Problem, K: int, checkpoint: int):
+        wv_c = wv.detach().contiguous()
+        om_c = omega.detach().contiguous().reshape(-1)
         state = initial_state(problem.op)
+        tape = problem.op.diff_tape(problem.cg_iters)
         saved = []
-        with torch.no_grad():
-            for t in range(K):
-                if t % checkpoint == 0:
-                    saved.append(tuple(s.clone() for s in state))
-                state = problem.iterate(state, wv, omega)
+        for t in range(K):
+            if t % checkpoint == 0:
+                saved.append([s.clone() for s in state])
+            state = problem.step(state, wv_c, om_c, tape)
         ctx.problem, ctx.K, ctx.checkpoint = problem, K, checkpoint
         ctx.saved_states = saved
         ctx.save_for_backward(wv, omega)
-        return state[0].clone()
+        n = problem.op.n
+        return state[0].reshape(n, n).clone()
 
     @staticmethod
     def backward(ctx, g_x):
         wv, omega = ctx.saved_tensors
         problem, K, C = ctx.problem, ctx.K, ctx.checkpoint
-        g_w = torch.zeros_like(wv)
-        g_om = torch.zeros_like(omega)
+        op = problem.op
+        wv_c = wv.detach().contiguous()
+        om_c = omega.detach().contiguous().reshape(-1)
+        w_bar = torch.zeros_like(wv_c)
+        om_bar = torch.zeros_like(om_c)
         # adjoint of the state after iteration K: only x_hat is an output
-        adj = None
+        bar = [torch.zeros(n, dtype=torch.complex64, device=op.device) for n in op.diff_state_shapes()]
+        bar[0] = g_x.detach().to(torch.complex64).contiguous().reshape(-1).clone()
         for seg in reversed(range(len(ctx.saved_states))):
             t0 = seg * C
             t1 = min(K, t0 + C)
-            with torch.enable_grad():
-                st = tuple(s.detach().requires_grad_(True) for s in ctx.saved_states[seg])
-                w_ = wv.detach().requires_grad_(True)
-                o_ = omega.detach().requires_grad_(True)
-                cur = st
-                for _ in range(t0, t1):
-                    cur = problem.iterate(cur, w_, o_)
-                if adj is None:
-                    outs, grads = [cur[0]], [g_x]
-                else:
-                    outs = [c for c, a in zip(cur, adj) if a is not None]
-                    grads = [a for a in adj if a is not None]
-                got = torch.autograd.grad(outs, list(st) + [w_, o_], grads, allow_unused=True)
-            adj = list(got[:len(st)])
-            if got[len(st)] is not None:
-                g_w += got[len(st)]
-            if got[len(st) + 1] is not None:
-                g_om += got[len(st) + 1]
+            states, tapes = [], []
+            cur = ctx.saved_states[seg]
+            for _ in range(t0, t1):
+                tape = op.diff_tape(problem.cg_iters)
+                states.append(cur)
+                tapes.append(tape)
+                cur = problem.step(cur, wv_c, om_c, tape)
+            for st, tape in zip(reversed(states), reversed(tapes)):
+                bar = problem.step_vjp(st, tape, bar, wv_c, om_c, w_bar, om_bar)
+            del states, tapes
         ctx.saved_states = None
-        return g_w, g_om, None, None, None
+        return w_bar.reshape(wv.shape), om_bar.reshape(omega.shape), None, None, None
 
 
 def sdmm_unrolled(op: binding.Context, y: torch.Tensor, eps: float, wv: torch.Tensor, omega: torch.Tensor,

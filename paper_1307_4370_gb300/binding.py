@@ -102,6 +102,16 @@ _SIGS = {
     "purify_sdmm_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "purify_sdmm_export": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "purify_sdmm_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "purify_diff_penalty": (_i32, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _vp]),
+    "purify_diff_tape_bytes": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "purify_diff_iteration": (_i32, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
+                                     ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
+    "purify_diff_iteration_vjp": (_i32, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i32,
+                                         ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                         _vp, _vp, _vp]),
+    "purify_vjp_soft_threshold": (_i32, [_i64, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp]),
+    "purify_vjp_l2ball": (_i32, [_vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]),
+    "purify_vjp_positive": (_i32, [_i64, _vp, _vp, _vp, _vp]),
     "purify_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "purify_profile_collect": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(_i32)]),
@@ -168,6 +178,25 @@ def _c64(t: torch.Tensor, n: int, what: str) -> torch.Tensor:
         raise ValueError(f"{what}: expected {n} complex64 values on a CUDA device, got "
                          f"{t.dtype} {tuple(t.shape)} on {t.device}")
     return t.contiguous()
+
+
+def _f32(t: torch.Tensor, n: int, what: str) -> torch.Tensor:
+    if t.dtype != torch.float32 or not t.is_cuda or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{what}: expected {n} contiguous float32 values on a CUDA device, got "
+                         f"{t.dtype} {tuple(t.shape)} on {t.device}")
+    return t
+
+
+def _ptr_array(ts, sizes):
+    """A C array of the device pointers of complex64 tensors of the given sizes."""
+    if len(ts) != len(sizes):
+        raise ValueError(f"expected {len(sizes)} arrays")
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, (t, n) in enumerate(zip(ts, sizes)):
+        if t.dtype != torch.complex64 or not t.is_cuda or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"state array {i}: expected {n} contiguous complex64 values on a CUDA device")
+        arr[i] = t.data_ptr()
+    return arr
 
 
 # ---------------------------------------------------------------------------
@@ -331,6 +360,55 @@ class Context:
             out.append((nm, int(launches[k]), float(ms[k])))
         return out
 
+    # differentiation (reverse mode of one SDMM iteration) -----------------
+    def diff_penalty(self, y: torch.Tensor, wvis: torch.Tensor, beta: float = 1e-3, stream=None) -> float:
+        """purify_diff_penalty: gamma = beta ||Psi^H Phi_w^H y_w||_inf."""
+        out = ctypes.c_double()
+        _check("purify_diff_penalty", self.lib.purify_diff_penalty(
+            self.ctx, _ptr(_c64(y, self.M, "y")), _ptr(_f32(wvis, self.M, "w")), float(beta), ctypes.byref(out),
+            _stream(stream)))
+        return out.value
+
+    def diff_tape(self, cg_iters: int) -> torch.Tensor:
+        """Device buffer for the tape of one differentiable iteration."""
+        nb = ctypes.c_size_t()
+        _check("purify_diff_tape_bytes", self.lib.purify_diff_tape_bytes(self.ctx, int(cg_iters), ctypes.byref(nb)))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+
+    def diff_state_shapes(self) -> list:
+        """Sizes of the seven state arrays (x_hat, z1, z2, z3, x1, x2, x3)."""
+        return [self.N, self.D, self.M, self.N, self.N, self.N, self.N]
+
+    def diff_iteration(self, y, wvis, omega, gamma: float, eps: float, cg_iters: int, state_in, state_out, tape,
+                       stream=None) -> None:
+        """purify_diff_iteration: state_out = one SDMM iteration of state_in, tape filled."""
+        sin = _ptr_array(state_in, self.diff_state_shapes())
+        sout = _ptr_array(state_out, self.diff_state_shapes())
+        _check("purify_diff_iteration", self.lib.purify_diff_iteration(
+            self.ctx, _ptr(_c64(y, self.M, "y")), _ptr(_f32(wvis, self.M, "w")), _ptr(_f32(omega, self.D, "omega")),
+            float(gamma), float(eps), int(cg_iters), sin, sout, _ptr(tape), _stream(stream)))
+
+    def diff_iteration_vjp(self, y, wvis, omega, gamma: float, eps: float, cg_iters: int, state_in, tape,
+                           bar_out, bar_in, wvis_bar, omega_bar, stream=None) -> None:
+        """purify_diff_iteration_vjp: adjoints of the inputs from those of the outputs;
+        adds to wvis_bar and omega_bar."""
+        shapes = self.diff_state_shapes()
+        _check("purify_diff_iteration_vjp", self.lib.purify_diff_iteration_vjp(
+            self.ctx, _ptr(_c64(y, self.M, "y")), _ptr(_f32(wvis, self.M, "w")), _ptr(_f32(omega, self.D, "omega")),
+            float(gamma), float(eps), int(cg_iters), _ptr_array(state_in, shapes), _ptr(tape),
+            _ptr_array(bar_out, shapes), _ptr_array(bar_in, shapes), _ptr(_f32(wvis_bar, self.M, "w_bar")),
+            _ptr(_f32(omega_bar, self.D, "omega_bar")), _stream(stream)))
+
+    def vjp_l2ball(self, a: torch.Tensor, y: torch.Tensor, eps: float, rbar: torch.Tensor, stream=None):
+        """purify_vjp_l2ball: (abar, ybar)."""
+        n = a.numel()
+        abar = torch.empty_like(a)
+        ybar = torch.empty_like(a)
+        _check("purify_vjp_l2ball", self.lib.purify_vjp_l2ball(
+            self.ctx, n, _ptr(_c64(a, n, "a")), _ptr(_c64(y, n, "y")), float(eps), _ptr(_c64(rbar, n, "rbar")),
+            _ptr(abar), _ptr(ybar), _stream(stream)))
+        return abar, ybar
+
     # SDMM ----------------------------------------------------------------
     def sdmm_state(self) -> "SdmmState":
         return SdmmState(self)
@@ -349,6 +427,28 @@ class Context:
                self.lib.purify_sdmm_solve(self.ctx, _ptr(y), float(eps), ctypes.byref(p), _ptr(out),
                                           ctypes.byref(rep), _stream(stream)))
         return out, rep.as_dict()
+
+
+def vjp_soft_threshold(a: torch.Tensor, w, gamma: float, rbar: torch.Tensor, wbar=None, stream=None):
+    """purify_vjp_soft_threshold: abar (and wbar += gamma dL/dlam when given)."""
+    lib = load()
+    n = a.numel()
+    abar = torch.empty_like(a)
+    _check("purify_vjp_soft_threshold", lib.purify_vjp_soft_threshold(
+        n, _ptr(_c64(a, n, "a")), _ptr(_f32(w, n, "w")) if w is not None else None, float(gamma),
+        _ptr(_c64(rbar, n, "rbar")), _ptr(abar), _ptr(_f32(wbar, n, "wbar")) if wbar is not None else None,
+        _stream(stream)))
+    return abar
+
+
+def vjp_positive(a: torch.Tensor, rbar: torch.Tensor, stream=None):
+    """purify_vjp_positive: abar."""
+    lib = load()
+    n = a.numel()
+    abar = torch.empty_like(a)
+    _check("purify_vjp_positive", lib.purify_vjp_positive(n, _ptr(_c64(a, n, "a")), _ptr(_c64(rbar, n, "rbar")),
+                                                          _ptr(abar), _stream(stream)))
+    return abar
 
 
 def launch_count() -> int:

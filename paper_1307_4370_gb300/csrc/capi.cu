@@ -262,7 +262,7 @@ unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_twp[0], c->d_twp[1], c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_diff, c->d_twp[0], c->d_twp[1], c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};

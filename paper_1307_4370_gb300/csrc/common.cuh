@@ -247,6 +247,7 @@ struct purify_ctx {
   int n, L, J, levels, q;
   int kernel;           // PURIFY_KERNEL_KB or PURIFY_KERNEL_GAUSS
   float2* d_tv;         // 7 N scratch of the TV prox (input, two dual pairs ping-ponged, last dual pair)
+  float2* d_diff;       // scratch of the differentiation calls (3 M + 4 N + D), allocated on first use
   float* d_beam;        // primary beam B (N floats), allocated by the first purify_set_beam
   bool beam_on;         // B applied (otherwise B = I)
   int beam_version;     // bumped by every purify_set_beam (graphs re-capture)
