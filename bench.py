@@ -40,6 +40,7 @@ from paper_1307_4370_gb300 import inputs  # noqa: E402
 REWEIGHT_EVERY = 60
 ROUNDS = 5
 L2_FLUSH_BYTES = 512 << 20
+QUALITY_ITERS = 60
 METRIC = "SDMM-SARA iterations/sec"
 UNIT = "iterations/s"
 
@@ -52,6 +53,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sdmm1024", choices=sorted(inputs.WORKLOADS) + ["batch32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the equal-iteration SNR of c64 and bf16 y")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-problem batched measurement")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--kernel", choices=["kb", "gauss"], default="kb",
                     help="interpolation kernel of G: Kaiser-Bessel or the paper's Gaussian")
@@ -443,6 +446,32 @@ def run_gpu(args, w):
     e2e_value = world * e2e_steps / max(e2e_s - e2e_steps * flush_s, 1e-9)
     clocks = sampler.stop()
 
+    # --- final-image SNR of the two storage forms of y at equal iteration count
+    quality = None
+    if rank == 0 and not args.no_quality:
+        x_true_r = torch.tensor(p.x_true.astype(np.float32), device=dev)
+        quality = {"iterations": QUALITY_ITERS}
+        for form in ("c64", "bf16"):
+            sq = ctx.sdmm_state()
+            if args.prior == "tv":
+                sq.set_prior("tv")
+            sq.init(y, eps, cg_iters=w.cg_iters)
+            if args.blocks > 0:
+                sq.set_blocks(*block_table(w.M, args.blocks, eps, binding.l2_bound))
+            if form == "bf16":
+                sq.set_data_bf16(y)
+            for _ in range(QUALITY_ITERS):
+                sq.step()
+            quality[f"snr_db_{form}"] = snr_db(x_true_r, sq.get_image().reshape(w.n, w.n))
+            sq.close()
+        quality["note"] = ("SNR = 20 log10(||x|| / ||x - Re x_hat||) (§6) after the same number of SDMM iterations "
+                           "from x_hat = 0, complex64 y and bf16-stored y with FP32 scales per 4096")
+
+    # --- 32 uneven problems batched (the batching workload), on rank 0 ------
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = measure_batch(min(args.steps, 20), 3)
+
     # --- per-kernel times (profiled steps) and the roofline ---------------
     ctx.profile_enable(True)
     prof_steps = min(args.steps, 30)
@@ -482,6 +511,8 @@ def run_gpu(args, w):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
                     "d2h_bytes_per_step": 8 * w.n * w.n},
             "gpu_launches": gpu_launches,
+            "quality": quality,
+            "batch32": batch,
             "clocks": clocks,
         }
         print(json.dumps(out), flush=True)
@@ -489,32 +520,47 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
-def run_batch(args):
+def snr_db(x_true, x_hat) -> float:
+    """Reconstruction SNR of §6, 20 log10(||x|| / ||x - x_hat||), of the real image."""
+    import torch
+
+    xr = x_hat.real.double() if torch.is_complex(x_hat) else x_hat.double()
+    xt = x_true.double()
+    return float(20.0 * torch.log10(torch.linalg.vector_norm(xt) / torch.linalg.vector_norm(xt - xr)).item())
+
+
+def measure_batch(steps: int, warmup: int) -> dict:
     """32 uneven problems advanced together (one CUDA graph per batch iteration)
-    against the same problems stepped one after another."""
+    against the same problems stepped one after another; final-image SNRs of
+    both (the batch only changes the schedule, so the iterates are equal)."""
     import torch
 
     from paper_1307_4370_gb300 import binding
 
-    torch.cuda.set_device(0)
     ws = inputs.batch_workloads(32)
-    states = []
-    for w in ws:
-        p = inputs.make_problem(w)
-        ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
-        y0 = ctx.phi(torch.tensor(p.x_true.astype(np.complex64), device="cuda"))
-        sig = float(torch.linalg.vector_norm(y0).item()) / math.sqrt(w.M) * 10 ** (-w.isnr_db / 20)
-        y = y0 + sig * torch.tensor(p.noise_unit.astype(np.complex64), device="cuda")
-        st = ctx.sdmm_state()
-        st.init(y, binding.l2_bound(w.M, sig), cg_iters=w.cg_iters)
-        states.append(st)
+
+    def make_states():
+        out = []
+        for w in ws:
+            p = inputs.make_problem(w)
+            ctx = binding.Context(w.n, p.uv.astype(np.float32), J=w.J)
+            xt = torch.tensor(p.x_true.astype(np.complex64), device="cuda")
+            y0 = ctx.phi(xt)
+            sig = float(torch.linalg.vector_norm(y0).item()) / math.sqrt(w.M) * 10 ** (-w.isnr_db / 20)
+            y = y0 + sig * torch.tensor(p.noise_unit.astype(np.complex64), device="cuda")
+            st = ctx.sdmm_state()
+            st.init(y, binding.l2_bound(w.M, sig), cg_iters=w.cg_iters)
+            out.append((ctx, st, torch.tensor(p.x_true.astype(np.float32), device="cuda")))
+        return out
+
+    K = max(1, min(steps, 50))
+    W = max(3, warmup)
+    made = make_states()
+    states = [st for _, st, _ in made]
     batch = binding.Batch(states)
-    batch.step(max(3, args.warmup))
-    for st in states:
-        st.step()
+    batch.step(W)
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    K = max(1, min(args.steps, 50))
     torch.cuda.synchronize()
     l0 = binding.launch_count()
     a.record(stream)
@@ -523,23 +569,48 @@ def run_batch(args):
     torch.cuda.synchronize()
     launches = binding.launch_count() - l0
     batched_ms = a.elapsed_time(b)
+    snr_b = [snr_db(xt, st.get_image().reshape(xt.shape)) for _, st, xt in made]
+    batch.close()
+    # the same problems, fresh, stepped one after another with their own graphs
+    made2 = make_states()
+    for _ in range(W):
+        for _, st, _ in made2:
+            st.step()
+    torch.cuda.synchronize()
     a.record(stream)
     for _ in range(K):
-        for st in states:
+        for _, st, _ in made2:
             st.step()
     b.record(stream)
     torch.cuda.synchronize()
     seq_ms = a.elapsed_time(b)
+    snr_s = [snr_db(xt, st.get_image().reshape(xt.shape)) for _, st, xt in made2]
     total_iters = K * len(ws)
-    out = {"metric": "SDMM-SARA instance-iterations/sec (32 uneven problems)", "value": total_iters / (batched_ms / 1e3),
-           "unit": "instance-iterations/s", "n_gpus": 1, "steps": K, "warmup": max(3, args.warmup),
-           "ms_per_step": batched_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    return {"value": total_iters / (batched_ms / 1e3), "unit": "instance-iterations/s", "steps": K, "warmup": W,
+            "ms_per_step": batched_ms / K, "gpu_launches": launches,
+            "sizes": [[w.n, w.M, w.J] for w in ws],
+            "snr_db_mean": float(np.mean(snr_b)),
+            "sequential": {"value": total_iters / (seq_ms / 1e3), "unit": "instance-iterations/s",
+                           "snr_db_mean": float(np.mean(snr_s)),
+                           "note": "same problems, one CUDA-graph step per problem in turn"},
+            "l2": "not flushed (one graph per batch iteration)"}
+
+
+def run_batch(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    r = measure_batch(args.steps, args.warmup)
+    out = {"metric": "SDMM-SARA instance-iterations/sec (32 uneven problems)", "value": r["value"],
+           "unit": r["unit"], "n_gpus": 1, "steps": r["steps"], "warmup": r["warmup"],
+           "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batch32: 32 problems, n in {128,192,256,384,512}, M in [0.2N, 2N], J in {4,6}",
-                      "sizes": [[w.n, w.M, w.J] for w in ws], "l2": "not flushed (one graph per batch iteration)"},
-           "sequential": {"value": total_iters / (seq_ms / 1e3), "unit": "instance-iterations/s",
-                          "note": "same problems, one CUDA-graph step per problem in turn"},
-           "gpu_launches": launches}
+                      "sizes": r["sizes"], "l2": r["l2"]},
+           "quality": {"snr_db_mean_batched": r["snr_db_mean"],
+                       "snr_db_mean_sequential": r["sequential"]["snr_db_mean"],
+                       "iterations": r["steps"] + r["warmup"]},
+           "sequential": r["sequential"], "gpu_launches": r["gpu_launches"]}
     print(json.dumps(out), flush=True)
 
 

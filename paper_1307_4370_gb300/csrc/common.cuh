@@ -16,11 +16,18 @@ namespace purify {
 // ---------------------------------------------------------------------------
 // Small complex helpers (float2 = complex64).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// The (re, im) pair is one 64-bit register pair: the packed FP32x2
+// instructions of sm_100+ (one FADD2 / FMUL2 / FFMA2 per complex add, scale
+// or real-by-complex FMA) round each component exactly as the scalar
+// instruction would, so these are bit-identical to the scalar forms.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+// y + s x (s real)
+__device__ __forceinline__ float2 caxpy(float s, float2 x, float2 y) { return __ffma2_rn(make_float2(s, s), x, y); }
+// a b = a.x (b.x, b.y) + a.y (-b.y, b.x)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  return __ffma2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), b));
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 

@@ -72,17 +72,15 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
     float2 acc = make_float2(0.f, 0.f);
     if (dr < T && dc < T) {
       const float2* base = halo + dr * W + dc;
+      float2 wcc[J];  // the column weights as (w, w) pairs for the FFMA2s
+#pragma unroll
+      for (int b = 0; b < J; ++b) wcc[b] = make_float2(wc[b], wc[b]);
 #pragma unroll
       for (int aa = 0; aa < J; ++aa) {
         float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int b = 0; b < J; ++b) {
-          const float2 g = base[aa * W + b];
-          t.x = fmaf(wc[b], g.x, t.x);
-          t.y = fmaf(wc[b], g.y, t.y);
-        }
-        acc.x = fmaf(wr[aa], t.x, acc.x);
-        acc.y = fmaf(wr[aa], t.y, acc.y);
+        for (int b = 0; b < J; ++b) t = __ffma2_rn(wcc[b], base[aa * W + b], t);
+        acc = caxpy(wr[aa], t, acc);
       }
     } else {
       // not in this tile (never for a consistent table): read the grid directly
@@ -265,17 +263,15 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
         const int kr = quot_small(le[q].y, inv_w), kc = le[q].y - kr * W;  // footprint start in the halo
         const float2* base = halo + kr * HW + kc;
         float2 acc = make_float2(0.f, 0.f);
+        float2 wcc[J];
+#pragma unroll
+        for (int b = 0; b < J; ++b) wcc[b] = make_float2(wc[b], wc[b]);
 #pragma unroll
         for (int aa = 0; aa < J; ++aa) {
           float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int b = 0; b < J; ++b) {
-            const float2 g = base[aa * HW + b];
-            t.x = fmaf(wc[b], g.x, t.x);
-            t.y = fmaf(wc[b], g.y, t.y);
-          }
-          acc.x = fmaf(wr[aa], t.x, acc.x);
-          acc.y = fmaf(wr[aa], t.y, acc.y);
+          for (int b = 0; b < J; ++b) t = __ffma2_rn(wcc[b], base[aa * HW + b], t);
+          acc = caxpy(wr[aa], t, acc);
         }
         val[q] = acc;
       }
@@ -360,11 +356,12 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
           const float* w = wt + ee * S;
           const float wr0 = w[ar], wr1 = w[ar + 1];
           const float wc0 = w[J + 2 + bc], wc1 = w[J + 3 + bc];
-          const float2 v0 = make_float2(wr0 * v.x, wr0 * v.y), v1 = make_float2(wr1 * v.x, wr1 * v.y);
-          a.a00.x = fmaf(wc0, v0.x, a.a00.x); a.a00.y = fmaf(wc0, v0.y, a.a00.y);
-          a.a01.x = fmaf(wc1, v0.x, a.a01.x); a.a01.y = fmaf(wc1, v0.y, a.a01.y);
-          a.a10.x = fmaf(wc0, v1.x, a.a10.x); a.a10.y = fmaf(wc0, v1.y, a.a10.y);
-          a.a11.x = fmaf(wc1, v1.x, a.a11.x); a.a11.y = fmaf(wc1, v1.y, a.a11.y);
+          const float2 v0 = cscale(v, wr0), v1 = cscale(v, wr1);
+          const float2 c0 = make_float2(wc0, wc0), c1 = make_float2(wc1, wc1);
+          a.a00 = __ffma2_rn(c0, v0, a.a00);
+          a.a01 = __ffma2_rn(c1, v0, a.a01);
+          a.a10 = __ffma2_rn(c0, v1, a.a10);
+          a.a11 = __ffma2_rn(c1, v1, a.a11);
         }
       }
     }

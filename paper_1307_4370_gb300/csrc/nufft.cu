@@ -120,11 +120,11 @@ struct RowFwdSrc {
     } else {
       float2 pp = o.r, ss = o.w;
       if (!first) {
-        pp = make_float2(fmaf(beta, o.p.x, o.r.x), fmaf(beta, o.p.y, o.r.y));
-        ss = make_float2(fmaf(beta, o.s.x, o.w.x), fmaf(beta, o.s.y, o.w.y));
+        pp = caxpy(beta, o.p, o.r);
+        ss = caxpy(beta, o.s, o.w);
       }
-      const float2 xx = make_float2(fmaf(alpha, pp.x, o.x.x), fmaf(alpha, pp.y, o.x.y));
-      const float2 rn = make_float2(fmaf(-alpha, ss.x, o.r.x), fmaf(-alpha, ss.y, o.r.y));
+      const float2 xx = caxpy(alpha, pp, o.x);
+      const float2 rn = caxpy(-alpha, ss, o.r);
       a.p[o.off] = pp;
       a.s[o.off] = ss;
       a.x[o.off] = xx;
@@ -306,7 +306,7 @@ struct RowInvDst {
       a.out[o.off] = v;
     } else if (MODE == kRowOutCgQ) {
       const float2 p = o.p;
-      const float2 q = make_float2(fmaf(2.f, p.x, v.x), fmaf(2.f, p.y, v.y));
+      const float2 q = caxpy(2.f, p, v);
       a.out[o.off] = q;
       part[0].add_prod(p.x, p.x);  // <r, r>
       part[0].add_prod(p.y, p.y);

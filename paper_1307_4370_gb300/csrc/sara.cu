@@ -98,12 +98,13 @@ __device__ __forceinline__ float dwt_plane(const float2* __restrict__ in, int in
   extern __shared__ float2 sm[];
   constexpr int taps = 2 * P;
   constexpr int hoff = P * (P - 1);  // db_p starts after db_1 .. db_(p-1): sum of 2q, q < p
-  float h[taps], g[taps];
+  float2 h[taps], g[taps];  // each tap as a (w, w) pair for the FFMA2s
 #pragma unroll
   for (int m = 0; m < taps; ++m) {
-    h[m] = wf.h[hoff + m];
+    const float hm = wf.h[hoff + m];
     const float hr = wf.h[hoff + taps - 1 - m];
-    g[m] = (m & 1) ? -hr : hr;
+    h[m] = make_float2(hm, hm);
+    g[m] = (m & 1) ? make_float2(-hr, -hr) : make_float2(hr, hr);
   }
   float f1 = 0.f;
   const int L = G.L, H = L / 2;
@@ -160,8 +161,8 @@ __device__ __forceinline__ float dwt_plane(const float2* __restrict__ in, int in
 #pragma unroll
     for (int m = 0; m < taps; ++m) {
       const float2 v = sp[m];
-      a.x = fmaf(h[m], v.x, a.x); a.y = fmaf(h[m], v.y, a.y);
-      d.x = fmaf(g[m], v.x, d.x); d.y = fmaf(g[m], v.y, d.y);
+      a = __ffma2_rn(h[m], v, a);
+      d = __ffma2_rn(g[m], v, d);
     }
     rowp[rr * (2 * TI) + i2] = a;
     rowp[rr * (2 * TI) + TI + i2] = d;
@@ -186,8 +187,8 @@ __device__ __forceinline__ float dwt_plane(const float2* __restrict__ in, int in
 #pragma unroll
       for (int m = 0; m < taps; ++m) {
         const float2 v = cp[m * (2 * TI)];
-        lo.x = fmaf(h[m], v.x, lo.x); lo.y = fmaf(h[m], v.y, lo.y);
-        hi.x = fmaf(g[m], v.x, hi.x); hi.y = fmaf(g[m], v.y, hi.y);
+        lo = __ffma2_rn(h[m], v, lo);
+        hi = __ffma2_rn(g[m], v, hi);
       }
     }
     lov[t] = lo;
@@ -314,12 +315,13 @@ __device__ __forceinline__ void idwt_filter(const float2* LLs, const float2* HLs
                                             float2* __restrict__ ll_out, float2 (&accum)[kIdwtMaxOut]) {
   constexpr int taps = 2 * P;
   constexpr int hoff = P * (P - 1);
-  float h[taps], g[taps];
+  float2 h[taps], g[taps];  // (w, w) pairs
 #pragma unroll
   for (int m = 0; m < taps; ++m) {
-    h[m] = wf.h[hoff + m];
+    const float hm = wf.h[hoff + m];
     const float hr = wf.h[hoff + taps - 1 - m];
-    g[m] = (m & 1) ? -hr : hr;
+    h[m] = make_float2(hm, hm);
+    g[m] = (m & 1) ? make_float2(-hr, -hr) : make_float2(hr, hr);
   }
   const int L = G.L;
   const int TO = G.tile;
@@ -338,13 +340,11 @@ __device__ __forceinline__ void idwt_filter(const float2* LLs, const float2* HLs
 #pragma unroll
       for (int u = 0; u < P; ++u) {
         const int t1 = tb - u;
-        const float hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
+        const float2 hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
         const float2 ll = LLs[t1 * CW + t2], hl = HLs[t1 * CW + t2];
         const float2 lh = LHs[t1 * CW + t2], hh = HHs[t1 * CW + t2];
-        av.x = fmaf(hm, ll.x, fmaf(gm, hl.x, av.x));
-        av.y = fmaf(hm, ll.y, fmaf(gm, hl.y, av.y));
-        dv.x = fmaf(hm, lh.x, fmaf(gm, hh.x, dv.x));
-        dv.y = fmaf(hm, lh.y, fmaf(gm, hh.y, dv.y));
+        av = __ffma2_rn(hm, ll, __ffma2_rn(gm, hl, av));
+        dv = __ffma2_rn(hm, lh, __ffma2_rn(gm, hh, dv));
       }
       As[idx] = av;
       Ds[idx] = dv;
@@ -362,10 +362,9 @@ __device__ __forceinline__ void idwt_filter(const float2* LLs, const float2* HLs
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const int t2 = tb - u;
-      const float hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
+      const float2 hm = par ? h[2 * u + 1] : h[2 * u], gm = par ? g[2 * u + 1] : g[2 * u];
       const float2 av = As[k1 * CW + t2], dv = Ds[k1 * CW + t2];
-      sacc.x = fmaf(hm, av.x, fmaf(gm, dv.x, sacc.x));
-      sacc.y = fmaf(hm, av.y, fmaf(gm, dv.y, sacc.y));
+      sacc = __ffma2_rn(hm, av, __ffma2_rn(gm, dv, sacc));
     }
     if (G.last) {
       accum[t] = cadd(accum[t], sacc);
