@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 using namespace purify;
@@ -259,6 +261,32 @@ __global__ void k_fill_f32(int64_t n, float* p, float v) {
 __global__ void k_sqrt_to(const double* src, double* dst) { *dst = sqrt(*src); }
 
 unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
+
+// TMA map of the forward grid whose box is one Gram-pass tile halo: float32
+// view, inner dimension 2 L floats, rows L; box of 2 grid_halo_ws(T, J)
+// floats by grid_halo_w(T, J) rows.  Encoded through the runtime's driver
+// entry point (no link against the driver library).  When the driver cannot
+// encode it, the Gram pass stages every halo with loads.
+void encode_halo_map(purify_ctx* c) {
+  c->halo_map_ok = 0;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return;
+  }
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * c->L, (cuuint64_t)c->L};
+  const cuuint64_t strides[1] = {(cuuint64_t)c->L * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * grid_halo_ws(c->tileT, c->J)), (cuuint32_t)grid_halo_w(c->tileT, c->J)};
+  const cuuint32_t estr[2] = {1, 1};
+  if (box[0] > 256 || box[1] > 256) return;
+  const CUresult r = encode(&c->halo_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->d_grid, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  c->halo_map_ok = (r == CUDA_SUCCESS) ? 1 : 0;
+}
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
@@ -574,6 +602,7 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PURIFY_E_CUDA);
   }
   if ((st = fft_prepare(c)) != PURIFY_OK) return fail(st);
+  encode_halo_map(c);
   if ((st = setup_visibilities(c, uv, s)) != PURIFY_OK) return fail(st);
   // shared memory above 48 KB needs an opt-in per kernel; sizes here stay below it
   *out = c;
@@ -1008,6 +1037,7 @@ int purify_sdmm_get_report(purify_ctx* c, purify_sdmm_state* st, purify_report* 
   cudaStream_t s = (cudaStream_t)stream;
   TRY_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   TRY_CUDA(cudaStreamSynchronize(s));
+  if (c->h_sc->dev_error) return PURIFY_E_TIMEOUT;
   rep->iters = st->iters;
   rep->f1 = c->h_sc->f1;
   rep->zeta = c->h_sc->zeta;

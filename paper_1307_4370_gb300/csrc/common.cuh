@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a SDMM-SARA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the map is encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
@@ -191,8 +192,11 @@ struct DevScalars {
   double cg_rho[2];   // gamma and alpha of CG steps j - 1 and j, by parity of j
   double cg_alpha[2];
   int cg_step_first;  // the step sizes in alpha, beta are those of a first step
+  int dev_error;      // nonzero when a bounded device wait gave up (reported as PURIFY_E_TIMEOUT)
   unsigned int counter[kNumCounters];
 };
+
+
 
 // Static plus dynamic shared memory above 48 KB needs a per-kernel opt-in
 // (the kernels' static shared memory is well under 8 KB).
@@ -232,8 +236,13 @@ __host__ __device__ constexpr int grid_wstride(int J) { return 2 * (J + 2) + 1; 
 __host__ __device__ constexpr size_t grid_entry_bytes(int J) { return 8 + 4 * (size_t)grid_wstride(J); }
 // The partial-sum slots share their space with the grid halo that the Gram
 // form (G^T G in one pass) stages before the entries.
+// Halo of the Gram form: T + 2(J - 1) rows of T + 2(J - 1) + 2 cells (the TMA
+// box starts one column early so that its first column is even, i.e. its
+// start 16-byte aligned, and its width stays even).
+__host__ __device__ constexpr int grid_halo_w(int T, int J) { return T + 2 * (J - 1); }
+__host__ __device__ constexpr int grid_halo_ws(int T, int J) { return T + 2 * (J - 1) + 2; }
 __host__ __device__ constexpr size_t grid_halo_bytes(int T, int J) {
-  return (size_t)(T + 2 * (J - 1)) * (T + 2 * (J - 1)) * 8;
+  return (size_t)grid_halo_w(T, J) * grid_halo_ws(T, J) * 8;
 }
 __host__ __device__ constexpr size_t grid_slot_bytes(int T, int J) {
   return grid_halo_bytes(T, J) > (size_t)2 * kGridThreads * 32 ? (grid_halo_bytes(T, J) + 15) / 16 * 16
@@ -302,6 +311,8 @@ struct purify_ctx {
   int4* d_dchunks;
 
   // scratch
+  CUtensorMap halo_map; // TMA map of d_grid: one box = the halo of one interior tile of the Gram pass
+  int halo_map_ok;      // the map was encoded (the Gram pass stages interior halos with TMA)
   float2* d_grid;       // L x L
   float2* d_grid2;      // L x L: output of the Gram pass (G^T G reads d_grid)
   float2* d_half;       // n x L (rows of the image after the row pass)

@@ -163,6 +163,50 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // on scheduling.
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) with an mbarrier, in inline PTX
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make the initialised barrier visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 2-D tiled copy of one box of the map at element coordinates (x, y) into
+// shared memory; completion is counted on the barrier in bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier, giving up after a bounded number of
+// polls (each poll may itself suspend the thread for a while); true when the
+// phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 struct Acc4 {  // a 2 x 2 block of complex sums
   float2 a00, a01, a10, a11;
 };
@@ -179,11 +223,13 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
                                                        const int* __restrict__ tile_nchunk,
                                                        unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
                                                        KbPoly kb, KappaScale ks, int L, int T, int tiles_1d,
-                                                       int chunk_max) {
+                                                       int chunk_max, const __grid_constant__ CUtensorMap halo_map,
+                                                       int use_tma, DevScalars* sc) {
   constexpr int NT = kGridThreads;
   constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
-  extern __shared__ float4 sm4[];
+  extern __shared__ __align__(128) float4 sm4[];
   __shared__ bool s_last;
+  __shared__ __align__(8) uint64_t s_bar;  // completion of the halo's TMA copy
   const int W = T + J - 1, HB = T / 2, NO = HB * HB;
   const int lhb = __ffs(HB) - 1;  // T is a power of two
   float4* part = sm4;  // slot j: first[j] at 4j, last[j] at 4j + 2 (Gram form: the halo first)
@@ -197,10 +243,29 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   const int ne = ch.z - ch.y;
   // ---- Gram form (G^T G): stage the (T + 2J - 2)^2 grid cells that the
   // footprints of the tile's entries cover; each entry's value is then its
-  // degridded sample, in the same order of operations as k_degrid
-  const int HW = T + 2 * (J - 1);
-  const float inv_hw = 1.0f / (float)HW, inv_w = 1.0f / (float)W;
+  // degridded sample, in the same order of operations as k_degrid.  The halo
+  // holds rows R0 - (J - 1) .. and columns from C0 - J (even, so that a copy
+  // starts 16-byte aligned), HWS = HW + 2 per row.  For a tile whose halo
+  // lies inside the grid one thread issues it as a TMA copy
+  // (cp.async.bulk.tensor) at kernel start, and it lands while the entries
+  // are being read; the halos of the outer ring of tiles wrap around the
+  // grid's edges and are loaded cell by cell.
+  const int HW = grid_halo_w(T, J), HWS = grid_halo_ws(T, J);
+  const float inv_hws = 1.0f / (float)HWS, inv_w = 1.0f / (float)W;
   float2* halo = reinterpret_cast<float2*>(sm4);
+  const bool tma = (MODE == kGridGram) && use_tma && R0 - (J - 1) >= 0 && R0 - (J - 1) + HW <= L &&
+                   C0 - J >= 0 && C0 - J + HWS <= L;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&s_bar, (unsigned)(HW * HWS * sizeof(float2)));
+      tma_load_2d(halo, &halo_map, 2 * (C0 - J), R0 - (J - 1), &s_bar);
+    }
+  }
   // this chunk's owner-work prefix (16-bit, set up with the lists; one
   // 16-byte group per thread for T <= 64), the first four list entries of
   // each thread, and the halo: all in flight together
@@ -214,25 +279,35 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
     le[q] = e < ne ? __ldg(&list[ch.y + e]) : make_int4(-1, 0, 0, 0);
   }
   if constexpr (MODE == kGridGram) {
-    for (int k0 = 0; k0 < HW * HW; k0 += 8 * NT) {
-      float2 v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + threadIdx.x + q * NT;
-        if (k < HW * HW) {
-          const int rr = quot_small(k, inv_hw), cc = k - rr * HW;
-          int r = R0 - (J - 1) + rr, c = C0 - (J - 1) + cc;
-          if (r < 0) r += L;
-          if (r >= L) r -= L;
-          if (c < 0) c += L;
-          if (c >= L) c -= L;
-          v[q] = __ldg(&Xin[(size_t)r * L + c]);
-        }
+    if (tma) {
+      // every thread waits for the copy (bounded: a copy that never lands
+      // sets the device error flag and the CTA leaves after a second wait)
+      if (!mbar_wait_bounded(&s_bar, 0)) {
+        if (threadIdx.x == 0) atomicOr(&sc->dev_error, 1);
+        mbar_wait_bounded(&s_bar, 0);
+        return;
       }
+    } else {
+      for (int k0 = 0; k0 < HW * HWS; k0 += 8 * NT) {
+        float2 v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + threadIdx.x + q * NT;
-        if (k < HW * HW) halo[k] = v[q];
+        for (int q = 0; q < 8; ++q) {
+          const int k = k0 + threadIdx.x + q * NT;
+          if (k < HW * HWS) {
+            const int rr = quot_small(k, inv_hws), cc = k - rr * HWS;
+            int r = R0 - (J - 1) + rr, c = C0 - J + cc;
+            if (r < 0) r += L;
+            if (r >= L) r -= L;
+            if (c < 0) c += L;
+            if (c >= L) c -= L;
+            v[q] = __ldg(&Xin[(size_t)r * L + c]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = k0 + threadIdx.x + q * NT;
+          if (k < HW * HWS) halo[k] = v[q];
+        }
       }
     }
     __syncthreads();
@@ -261,7 +336,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       kb_weights<J>(kb, __int_as_float(le[q].w), wc);
       if constexpr (MODE == kGridGram) {
         const int kr = quot_small(le[q].y, inv_w), kc = le[q].y - kr * W;  // footprint start in the halo
-        const float2* base = halo + kr * HW + kc;
+        const float2* base = halo + kr * HWS + kc + 1;  // the halo's first column is C0 - J
         float2 acc = make_float2(0.f, 0.f);
         float2 wcc[J];
 #pragma unroll
@@ -270,7 +345,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
         for (int aa = 0; aa < J; ++aa) {
           float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int b = 0; b < J; ++b) t = __ffma2_rn(wcc[b], base[aa * HW + b], t);
+          for (int b = 0; b < J; ++b) t = __ffma2_rn(wcc[b], base[aa * HWS + b], t);
           acc = caxpy(wr[aa], t, acc);
         }
         val[q] = acc;
@@ -456,7 +531,8 @@ static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cu
                       OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_chunk_tab, c->chunk_tab_stride,     \
                       c->d_items, c->d_item_row,                                                                \
                       c->d_tile_slot0, c->d_tile_nchunk,                                                        \
-                      c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max)));   \
+                      c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max,      \
+                      c->halo_map, c->halo_map_ok, c->d_sc)));                                                  \
   } while (0)
   if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
   else if (mode == kGridSorted) GRD(kGridSorted, "grid", c->d_grid, nullptr);
