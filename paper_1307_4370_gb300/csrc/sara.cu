@@ -44,28 +44,21 @@ struct BasisList {
 __device__ __forceinline__ float sara_prox_v(float2 al, float2 z, float w, size_t j, const SaraProxArgs& pa,
                                              float gamma) {
   const float2 a = cadd(al, z);
-  const float mag = sqrtf(a.x * a.x + a.y * a.y);
-  const float shrink = fmaxf(mag - gamma * w, 0.0f);
-  const float s = mag > 0.0f ? shrink / mag : 0.0f;
+  // shrink factor (|a| - lam)^+ / |a| = max(1 - lam / |a|, 0), with 1 / |a|
+  // from the hardware reciprocal square root (0 where a = 0)
+  const float m2 = fmaf(a.x, a.x, a.y * a.y);
+  const float s = m2 > 0.0f ? fmaxf(fmaf(-gamma * w, rsqrtf(m2), 1.0f), 0.0f) : 0.0f;
   const float2 r1 = cscale(a, s);
   const float2 z1n = csub(a, r1);
   pa.z1[j] = z1n;
   pa.u1[j] = csub(r1, z1n);
-  return w * sqrtf(fmaf(al.x, al.x, al.y * al.y));
+  const float al2 = fmaf(al.x, al.x, al.y * al.y);
+  return w * (al2 > 0.0f ? al2 * rsqrtf(al2) : 0.0f);
 }
 
 __device__ __forceinline__ float sara_prox(float2 al, size_t j, const SaraProxArgs& pa, float gamma) {
   const float w = pa.w ? pa.w[j] : 1.0f;
-  const float2 z = pa.z1[j];
-  const float2 a = cadd(al, z);
-  const float mag = sqrtf(a.x * a.x + a.y * a.y);
-  const float shrink = fmaxf(mag - gamma * w, 0.0f);
-  const float s = mag > 0.0f ? shrink / mag : 0.0f;
-  const float2 r1 = cscale(a, s);
-  const float2 z1n = csub(a, r1);
-  pa.z1[j] = z1n;
-  pa.u1[j] = csub(r1, z1n);
-  return w * sqrtf(fmaf(al.x, al.x, al.y * al.y));
+  return sara_prox_v(al, pa.z1[j], w, j, pa, gamma);
 }
 
 // ---------------------------------------------------------------------------
