@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -290,7 +291,7 @@ void encode_halo_map(purify_ctx* c) {
 
 void free_ctx(purify_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_diff, c->d_twp[0], c->d_twp[1], c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
+  void* ptrs[] = {c->d_dense_tiles, c->d_H, c->d_gram_chunks, c->d_diff, c->d_twp[0], c->d_twp[1], c->d_deapod, c->d_beam, c->d_tv, c->d_tw, c->d_uv, c->d_perm, c->d_list, c->d_chunks, c->d_chunk_tab, c->d_items, c->d_item_row, c->d_dchunks, c->d_tile_slot0,
                   c->d_tile_nchunk, c->d_tile_cnt, c->d_slots,
                   c->d_grid, c->d_grid2, c->d_half, c->d_vis, c->d_vis2, c->d_ll[0], c->d_ll[1], c->d_img[0],
                   c->d_img[1], c->d_img[2], c->d_img[3], c->d_partials, c->d_sc};
@@ -299,6 +300,71 @@ void free_ctx(purify_ctx* c) {
   if (c->h_sc) cudaFreeHost(c->h_sc);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   delete c;
+}
+
+// Tiles whose gridding lists hold more than this many entries per cell keep
+// G^T G as a stored stencil instead of gathering (measured on this GPU: the
+// stencil streams (2J - 1)^2 floats per cell from memory, the gather issues
+// ~1500 instructions per entry, and the two overlap in one launch).
+#ifndef PURIFY_DENSE_ENTRIES_PER_CELL
+#define PURIFY_DENSE_ENTRIES_PER_CELL 2.0
+#endif
+constexpr double kDenseEntriesPerCell = PURIFY_DENSE_ENTRIES_PER_CELL;
+
+// G^T G restricted to the cells of the dense tiles (§5: G^H G, precomputed
+// and stored, to speed up the CG solve): for cell k of tile t and offset d in
+// [-(J-1), J-1]^2, H[t][d][k] = sum over the tile's list entries m of
+// w_m(k) w_m(k + d), w_m the J x J interpolation weights of visibility m
+// (exact kernel values in double, at the fractions the device uses).  Every
+// visibility whose footprint covers a cell of the tile is on the tile's list,
+// so (G^T G X)(k) = sum_d H[t][d][k] X(k + d) exactly.  Built in double on
+// the host, one tile per thread of a small pool, and stored as float.
+void build_dense_gram(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
+                      const std::vector<int>& dense, std::vector<float>& H) {
+  const int T = c->tileT, J = c->J, W = T + J - 1, ND = (2 * J - 1) * (2 * J - 1), TT = T * T;
+  const double beta = kb_beta(J), i0b = std::cyl_bessel_i(0.0, beta);
+  H.assign((size_t)dense.size() * ND * TT, 0.0f);
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    std::vector<double> acc((size_t)ND * TT);
+    for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
+      const int t = dense[q];
+      std::fill(acc.begin(), acc.end(), 0.0);
+      for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
+        const int4 le = entries[e];
+        const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
+        float frf, fcf;
+        std::memcpy(&frf, &le.z, 4);
+        std::memcpy(&fcf, &le.w, 4);
+        double wr[kMaxJ], wc[kMaxJ];
+        for (int a = 0; a < J; ++a) {
+          wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+          wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+        }
+        for (int a = 0; a < J; ++a) {
+          const int r = kr - (J - 1) + a;
+          if (r < 0 || r >= T) continue;
+          for (int b = 0; b < J; ++b) {
+            const int cc = kc - (J - 1) + b;
+            if (cc < 0 || cc >= T) continue;
+            const double wk = wr[a] * wc[b];
+            double* hk = acc.data() + r * T + cc;
+            for (int a2 = 0; a2 < J; ++a2) {
+              const int drow = (a2 - a + J - 1) * (2 * J - 1) - b + J - 1;
+              for (int b2 = 0; b2 < J; ++b2) hk[(size_t)(drow + b2) * TT] += wk * wr[a2] * wc[b2];
+            }
+          }
+        }
+      }
+      float* out = H.data() + q * (size_t)ND * TT;
+      for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
+    }
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
 }
 
 // Visibility table: sort by the grid tile of the first footprint cell and
@@ -380,6 +446,40 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
     cudaMemcpyAsync(c->d_tile_nchunk, plan.nchunk.data(), c->ntiles * sizeof(int), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->d_tile_cnt, 0, c->ntiles * sizeof(unsigned), s);
     if (cudaStreamSynchronize(s) != cudaSuccess) st = PURIFY_E_CUDA;
+  }
+  // dense tiles of the Gram pass and their stored G^T G (see build_dense_gram)
+  if (st == PURIFY_OK) {
+    std::vector<int> dense;
+    std::vector<char> is_dense(c->ntiles, 0);
+    for (int t = 0; t < c->ntiles; ++t)
+      if ((double)(plan.list_off[t + 1] - plan.list_off[t]) > kDenseEntriesPerCell * T * T) {
+        dense.push_back(t);
+        is_dense[t] = 1;
+      }
+    std::vector<int> gram_chunks;
+    for (int q = 0; q < c->nchunks; ++q)
+      if (!is_dense[plan.chunks[q].x]) gram_chunks.push_back(q);
+    c->n_dense = (int)dense.size();
+    c->n_gram_chunks = (int)gram_chunks.size();
+    std::vector<float> H;
+    if (c->n_dense > 0) {
+      std::vector<int4> entries(c->nlist);
+      if (cudaMemcpy(entries.data(), c->d_list, c->nlist * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = PURIFY_E_CUDA;
+      if (st == PURIFY_OK) build_dense_gram(c, plan, entries, dense, H);
+    }
+    if (st == PURIFY_OK && ((st = dev_alloc(&c->d_dense_tiles, std::max(1, c->n_dense))) ||
+                            (st = dev_alloc(&c->d_gram_chunks, std::max(1, c->n_gram_chunks))) ||
+                            (st = dev_alloc(&c->d_H, std::max<size_t>(1, H.size())))))
+      ;
+    if (st == PURIFY_OK) {
+      if ((c->n_dense > 0 &&
+           (cudaMemcpy(c->d_dense_tiles, dense.data(), dense.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->d_H, H.data(), H.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)) ||
+          (c->n_gram_chunks > 0 && cudaMemcpy(c->d_gram_chunks, gram_chunks.data(), gram_chunks.size() * sizeof(int),
+                                              cudaMemcpyHostToDevice) != cudaSuccess))
+        st = PURIFY_E_CUDA;
+    }
   }
   cudaFree(d_lk);
   cudaFree(d_uv_user);

@@ -306,6 +306,15 @@ struct purify_ctx {
   unsigned* d_tile_cnt; // arrival counters (zero between launches)
   int nslots;
   float2* d_slots;      // nslots x tileT^2 partial tiles
+  // dense tiles of the Gram pass: G^T G stored per cell as a (2J - 1)^2
+  // stencil (§5 proposes precomputing G^H G for the CG solve), applied in the
+  // Gram launch's first n_dense CTAs; the other CTAs run the gather over the
+  // chunks of the remaining tiles (gram_chunks)
+  int n_dense;
+  int* d_dense_tiles;   // tile of each dense CTA
+  float* d_H;           // n_dense x (2J - 1)^2 x T^2: H[t][d][cell], d = (dr + J - 1)(2J - 1) + dc + J - 1
+  int n_gram_chunks;
+  int* d_gram_chunks;   // chunks of the tiles that are not dense
   // degridding work units: (tile, begin, end, -) runs of home visibilities
   int ndchunks;
   int4* d_dchunks;

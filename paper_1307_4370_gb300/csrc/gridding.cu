@@ -224,7 +224,10 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
                                                        unsigned* __restrict__ tile_cnt, float2* __restrict__ slots,
                                                        KbPoly kb, KappaScale ks, int L, int T, int tiles_1d,
                                                        int chunk_max, const __grid_constant__ CUtensorMap halo_map,
-                                                       int use_tma, DevScalars* sc) {
+                                                       int use_tma, DevScalars* sc, int n_dense,
+                                                       const int* __restrict__ dense_tiles,
+                                                       const float* __restrict__ H,
+                                                       const int* __restrict__ gram_chunks) {
   constexpr int NT = kGridThreads;
   constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
   extern __shared__ __align__(128) float4 sm4[];
@@ -236,7 +239,20 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   float2* yv = reinterpret_cast<float2*>(reinterpret_cast<char*>(sm4) + grid_slot_bytes(T, J));
   float* wt = reinterpret_cast<float*>(yv + chunk_max);
   int* P = reinterpret_cast<int*>(wt + (size_t)chunk_max * S);  // NO + 1 work prefix of the owners
-  const int4 ch = chunks[blockIdx.x];
+  // Gram form: the first n_dense CTAs apply the stored G^T G of one dense tile
+  // each; the others gather over the chunks of the remaining tiles
+  int q = blockIdx.x;  // this CTA's chunk
+  bool dense = false;
+  int dtile = 0;
+  if constexpr (MODE == kGridGram) {
+    if ((int)blockIdx.x < n_dense) {
+      dense = true;
+      dtile = dense_tiles[blockIdx.x];
+    } else {
+      q = gram_chunks[blockIdx.x - n_dense];
+    }
+  }
+  const int4 ch = dense ? make_int4(dtile, 0, 0, -1) : chunks[q];
   const int tile = ch.x;
   const int tr = tile / tiles_1d, tc = tile - tr * tiles_1d;
   const int R0 = tr * T, C0 = tc * T;
@@ -270,8 +286,8 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   // 16-byte group per thread for T <= 64), the first four list entries of
   // each thread, and the halo: all in flight together
   uint4 tv;
-  const uint4* tab4 = reinterpret_cast<const uint4*>(tab + (size_t)blockIdx.x * tab_stride);
-  if (threadIdx.x < tab_stride / 8) tv = __ldg(&tab4[threadIdx.x]);
+  const uint4* tab4 = reinterpret_cast<const uint4*>(tab + (size_t)q * tab_stride);
+  if (!dense && threadIdx.x < tab_stride / 8) tv = __ldg(&tab4[threadIdx.x]);
   int4 le[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -311,6 +327,29 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       }
     }
     __syncthreads();
+    if (dense) {
+      // (G^T G X)(k) = sum_d H[d][k] X(k + d) over the (2J - 1)^2 offsets, H
+      // streamed once per launch (coalesced over the cells), X from the halo
+      constexpr int NDW = 2 * J - 1;
+      const int TT = T * T, lt = lhb + 1;
+      const float* Ht = H + (size_t)blockIdx.x * NDW * NDW * TT;
+      for (int k = threadIdx.x; k < TT; k += NT) {
+        const int r = k >> lt, cc = k & (T - 1);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int dr = 0; dr < NDW; ++dr) {
+          const float2* hrow = halo + (r + dr) * HWS + cc + 1;
+          const float* hh = Ht + (size_t)dr * NDW * TT + k;
+          float hv[NDW];
+#pragma unroll
+          for (int dc = 0; dc < NDW; ++dc) hv[dc] = __ldcs(&hh[(size_t)dc * TT]);
+#pragma unroll
+          for (int dc = 0; dc < NDW; ++dc) acc = caxpy(hv[dc], hrow[dc], acc);
+        }
+        X[(size_t)(R0 + r) * L + C0 + cc] = acc;
+      }
+      return;
+    }
   }
   // ---- stage the chunk's entries (loads of four entries per thread in flight)
   for (int e0 = 0; e0 < ne; e0 += 4 * NT) {
@@ -394,7 +433,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   const int t0 = (j * Wt + NT - 1) / NT, t1 = ((j + 1) * Wt + NT - 1) / NT;
   const int nmy = t1 - t0;
   if (nmy > 0) {
-    const uint32_t* its = items + (size_t)item_row[blockIdx.x] * NT + j;
+    const uint32_t* its = items + (size_t)item_row[q] * NT + j;
     constexpr int PF = MINB >= 5 ? 4 : 8;  // items in flight per thread
     uint32_t pf[PF];
 #pragma unroll
@@ -527,12 +566,14 @@ static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cu
   do {                                                                                                         \
     allow_smem(k_grid<J, MD, MINB>, sm);                                                                       \
     PURIFY_LAUNCH(c, NAME, s,                                                                                  \
-                  (k_grid<J, MD, MINB><<<c->nchunks, kGridThreads, sm, s>>>(                                   \
+                  (k_grid<J, MD, MINB><<<MD == kGridGram ? c->n_dense + c->n_gram_chunks : c->nchunks,       \
+                                         kGridThreads, sm, s>>>(                                               \
                       OUT, IN, c->d_perm, vis, c->d_list, c->d_chunks, c->d_chunk_tab, c->chunk_tab_stride,     \
                       c->d_items, c->d_item_row,                                                                \
                       c->d_tile_slot0, c->d_tile_nchunk,                                                        \
                       c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max,      \
-                      c->halo_map, c->halo_map_ok, c->d_sc)));                                                  \
+                      c->halo_map, c->halo_map_ok, c->d_sc, c->n_dense, c->d_dense_tiles, c->d_H,             \
+                      c->d_gram_chunks)));                                                                      \
   } while (0)
   if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
   else if (mode == kGridSorted) GRD(kGridSorted, "grid", c->d_grid, nullptr);

@@ -183,3 +183,21 @@ def test_phi_and_adjoint_power_of_two_grids(n, M, J):
     ctx = binding.Context(n, uv.astype(np.float32), J=J, levels=4)
     assert rel_err(host(ctx.phi(dev(x, torch))), me.phi(x, uv, J)) <= TOL
     assert rel_err(host(ctx.phi_adj(dev(v, torch))), me.phi_adj(v, uv, n, J)) <= TOL
+
+
+@pytest.mark.parametrize("n,M,J,tile", [(64, 40000, 6, 16), (96, 60000, 4, 16), (128, 60000, 6, 32)])
+def test_cg_solve_dense_tiles(n, M, J, tile):
+    """Coverages dense enough (more than two list entries per grid cell in
+    the central tiles) that the Gram pass applies G^T G from its stored
+    per-cell stencils there and gathers elsewhere: CG against the oracle."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(n + M)
+    uv = inputs.uv_variable_density(M, n, rng).astype(np.float32).astype(np.float64)
+    ctx = binding.Context(n, uv.astype(np.float32), J=J, tile=tile)
+    b = inputs.random_image(n, rng)
+    x0 = inputs.random_image(n, rng)
+    x, _ = ctx.cg_solve(dev(b, torch), dev(x0, torch), 6)
+    want, _ = ocg.cg(lambda v: me.phi_adj(me.phi(v, uv, J), uv, n, J) + 2.0 * v, b, x0, 6)
+    assert rel_err(host(x).reshape(n, n), want) <= 1e-5
