@@ -251,7 +251,11 @@ __host__ __device__ constexpr size_t grid_slot_bytes(int T, int J) {
 __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
   return grid_slot_bytes(T, J) + (size_t)((T / 2) * (T / 2) + 1) * 4;
 }
-constexpr size_t kGridSmemBudget = 72 * 1024;
+// Shared-memory budget of one gridding CTA: the chunks of a tile's list are
+// sized so that the kernel fits 44 KB (five CTAs per SM, register-capped
+// build), which beats three larger CTAs per SM on this GPU: the gather is
+// latency-bound and more resident warps hide more of it.
+constexpr size_t kGridSmemBudget = 44 * 1024;
 // 16-bit per-chunk table of the gather: the NO + 1 owner-work prefix values
 // (stride rounded to 8 entries = 16 bytes)
 __host__ __device__ constexpr int grid_tab_stride(int T) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }

@@ -93,10 +93,10 @@ int build_gather_plan(const int* k0, const GatherPlanParams& prm, GatherPlan& ou
 
   // gridding work units: each tile's list in chunks whose entries, with the
   // kernel's fixed tables, fit the shared-memory budget (large tiles: room
-  // for at least 512 entries beyond the fixed part)
+  // for at least 256 entries beyond the fixed part)
   const int64_t mean = (nlist + ntiles - 1) / ntiles;
   const int64_t fixed = (int64_t)prm.fixed_bytes, per = (int64_t)prm.entry_bytes;
-  const int64_t budget = std::max<int64_t>((int64_t)prm.smem_budget, fixed + 512 * per);
+  const int64_t budget = std::max<int64_t>((int64_t)prm.smem_budget, fixed + 256 * per);
   const int cap = (int)std::max<int64_t>(128, (budget - fixed) / per / 32 * 32);
   out.chunk_max = (int)std::min<int64_t>(cap, std::max<int64_t>(256, ((3 * mean / 2 + 127) / 128) * 128));
   out.slot0.assign(ntiles, -1);
