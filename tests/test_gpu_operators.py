@@ -82,9 +82,12 @@ def test_phi_large_sampled():
         ctx.close()
 
 
+# Sizes from 8^2 (filters longer than the deep bands) to 1024^2, basis subsets
+# and level counts.
 @pytest.mark.parametrize("n,levels,mask", [(16, 4, 0x1FF), (64, 4, 0x1FF), (96, 4, 0x1FF), (192, 4, 0x1FF),
                                            (256, 4, 0x1FF), (64, 3, 0x100), (32, 2, 0x001), (64, 4, 0x0F5),
-                                           (8, 3, 0x1FF)])
+                                           (8, 3, 0x1FF), (384, 4, 0x1FF), (512, 4, 0x1FF), (1024, 4, 0x1FF),
+                                           (512, 2, 0x082), (1024, 3, 0x1FF)])
 def test_sara(n, levels, mask):
     torch = require_gpu()
     from paper_1307_4370_gb300 import binding
@@ -201,3 +204,20 @@ def test_cg_solve_dense_tiles(n, M, J, tile):
     x, _ = ctx.cg_solve(dev(b, torch), dev(x0, torch), 6)
     want, _ = ocg.cg(lambda v: me.phi_adj(me.phi(v, uv, J), uv, n, J) + 2.0 * v, b, x0, 6)
     assert rel_err(host(x).reshape(n, n), want) <= 1e-5
+
+
+def test_sara_contexts_of_different_sizes():
+    """Contexts of different sizes used in turn: a kernel's shared-memory
+    limit is a property of the kernel, shared by every context of the
+    process, so each launch must still get the size it needs."""
+    torch = require_gpu()
+    from paper_1307_4370_gb300 import binding
+
+    rng = np.random.default_rng(5)
+    big = binding.Context(512, inputs.uniform_uv(64, rng).astype(np.float32), J=4, levels=4)
+    small = binding.Context(64, inputs.uniform_uv(64, rng).astype(np.float32), J=4, levels=4)
+    for ctx, n in ((big, 512), (small, 64), (big, 512)):
+        x = inputs.random_image(n, rng)
+        al = host(ctx.sara_analysis(dev(x, torch)))
+        assert rel_err(al, osara.sara_analysis(x, 4)) <= TOL
+        assert rel_err(host(ctx.sara_synthesis(dev(al, torch))).reshape(n, n), osara.sara_synthesis(al, 4)) <= TOL
