@@ -474,14 +474,16 @@ struct RowOutArgs {
   float2* z3;           // sdmm
 };
 
+int fft_prepare(purify_ctx* c);  // tables of the power-of-two FFT engine (at context creation)
 // cg_j: in the CG modes, the CG step whose update this pass applies (its
 // inner-product partials are in the kCntDot slot).
-int fft_prepare(purify_ctx* c);  // tables of the power-of-two FFT engine (at context creation)
 int phi_forward_grid(purify_ctx* c, RowInMode mode, const RowInArgs& a, cudaStream_t s, int cg_j = 0);
 int cg_partial_blocks(const purify_ctx* c);
 // CG step sizes formed by the consuming kernels (few partials) or by a
-// one-block kernel after the inverse row pass (many partials).
-constexpr int kCgConsumeMaxBlocks = 256;
+// one-block kernel after the inverse row pass (many partials: at 256
+// partials, e.g. 1024^2, every block of the 1024-block forward row pass
+// summing them cost 9 us per CG step against ~2 us for the extra launch).
+constexpr int kCgConsumeMaxBlocks = 128;
 int cg_consumer_blocks(const purify_ctx* c);  // nblk for the consumers: the partial count, or 0
 int launch_cg_scalars(purify_ctx* c, int cg_j, cudaStream_t s);
 int degrid(purify_ctx* c, DegridOut mode, const DegridArgs& a, cudaStream_t s);

@@ -362,14 +362,30 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ half
 // compile-time engine of fft_p2.cuh: the zero padding of the forward passes
 // and the crop of the adjoint ones prune the first / last stage.
 // ---------------------------------------------------------------------------
+#ifndef P2_E_LARGE
+#define P2_E_LARGE 16
+#endif
+#ifndef P2_E_CG
+#define P2_E_CG 8
+#endif
+#ifndef P2_NS_COL
+#define P2_NS_COL (L == 2048 ? 8 : 4)  // at most 1024 threads: NS L / E
+#endif
+#ifndef P2_ROWCG_THREADS
+#define P2_ROWCG_THREADS 256
+#endif
+#ifndef P2_RINV_THREADS
+#define P2_RINV_THREADS 512
+#endif
 template <int L>
 struct P2Cfg {
-  static constexpr int E = L >= 1024 ? 16 : 8;                     // plain row, column and inverse row passes
-  static constexpr int E_CG = 8;                                   // forward row pass with the CG update
+  static constexpr int E = L >= 1024 ? P2_E_LARGE : 8;             // plain row, column and inverse row passes
+  static constexpr int E_CG = P2_E_CG;                             // forward row pass with the CG update
   static constexpr int NS_ROW = 256 / (L / E) > 0 ? 256 / (L / E) : 1;
-  static constexpr int NS_ROWCG = 256 / (L / E_CG) > 0 ? 256 / (L / E_CG) : 1;
-  static constexpr int NS_RINV = 512 / (L / E) > 0 ? (512 / (L / E) > 8 ? 8 : 512 / (L / E)) : 1;
-  static constexpr int NS_COL = 4;
+  static constexpr int NS_ROWCG = P2_ROWCG_THREADS / (L / E_CG) > 0 ? P2_ROWCG_THREADS / (L / E_CG) : 1;
+  static constexpr int NS_RINV =
+      P2_RINV_THREADS / (L / E) > 0 ? (P2_RINV_THREADS / (L / E) > 8 ? 8 : P2_RINV_THREADS / (L / E)) : 1;
+  static constexpr int NS_COL = P2_NS_COL;
 };
 
 template <int L, int E, int NSIG, int MODE>
