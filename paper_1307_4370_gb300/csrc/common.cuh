@@ -252,10 +252,15 @@ __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
   return grid_slot_bytes(T, J) + (size_t)((T / 2) * (T / 2) + 1) * 4;
 }
 // Shared-memory budget of one gridding CTA: the chunks of a tile's list are
-// sized so that the kernel fits 44 KB (five CTAs per SM, register-capped
-// build), which beats three larger CTAs per SM on this GPU: the gather is
-// latency-bound and more resident warps hide more of it.
-constexpr size_t kGridSmemBudget = 44 * 1024;
+// sized so that the kernel fits 56 KB (four CTAs per SM, a 64-register
+// build).  Measured at 1024^2 (Gram / gridding launch): 72 KB, three CTAs per
+// SM: 139 / 154 us; 44 KB, five: 131 / 154 us; 56 KB, four: 129.5 / 146 us.
+// The gather is latency-bound, so resident warps matter, but smaller chunks
+// split more tiles into several chunks (partial tiles and their merge).
+#ifndef PURIFY_GRID_SMEM_BUDGET_KB
+#define PURIFY_GRID_SMEM_BUDGET_KB 56
+#endif
+constexpr size_t kGridSmemBudget = PURIFY_GRID_SMEM_BUDGET_KB * 1024;
 // 16-bit per-chunk table of the gather: the NO + 1 owner-work prefix values
 // (stride rounded to 8 entries = 16 bytes)
 __host__ __device__ constexpr int grid_tab_stride(int T) { return ((T / 2) * (T / 2) + 1 + 7) / 8 * 8; }

@@ -483,12 +483,22 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
   }
   __syncthreads();
   // ---- owners cut by slice ends (sum in slice order) and owners with no work
+  const float inv_wt = Wt > 0 ? 1.0f / (float)Wt : 0.f;
   for (int o = threadIdx.x; o < NO; o += NT) {
     const int Po = P[o], Pe = P[o + 1];
     Acc4 a;
     a.a00 = a.a01 = a.a10 = a.a11 = make_float2(0.f, 0.f);
     if (Pe > Po) {
-      const int ja = (Po * NT) / Wt, jb = ((Pe - 1) * NT) / Wt;
+      // slices holding the owner's first and last step: floor(P NT / Wt),
+      // through a float reciprocal (the quotient is at most NT, so the
+      // product is within one of it) and one integer correction
+      auto slice_of = [&](int x) {
+        int qq = __float2int_rz((float)x * inv_wt);
+        if (qq * Wt > x) --qq;
+        else if ((qq + 1) * Wt <= x) ++qq;
+        return qq;
+      };
+      const int ja = slice_of(Po * NT), jb = slice_of((Pe - 1) * NT);
       if (ja == jb) continue;  // written by its slice
       float4 p0 = part[4 * ja + 2], p1 = part[4 * ja + 3];
       for (int jj = ja + 1; jj <= jb; ++jj) {
@@ -557,9 +567,9 @@ static size_t grid_smem(const purify_ctx* c) {
   return grid_fixed_bytes(c->tileT, J) + (size_t)c->chunk_max * grid_entry_bytes(J);
 }
 
-// Chunks small enough for five resident CTAs per SM take the build with a
-// register cap that allows five; larger ones (three per SM by shared memory)
-// keep more registers.
+// Chunks small enough for five (four) resident CTAs per SM take the build
+// with a register cap that allows five (four); larger ones (three per SM by
+// shared memory) keep more registers.
 template <int J, int MINB>
 static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cudaStream_t s) {
 #define GRD(MD, NAME, OUT, IN)                                                                                 \
@@ -585,6 +595,7 @@ template <int J>
 static void grid_J(purify_ctx* c, GridIn mode, const float2* vis, cudaStream_t s) {
   const size_t sm = grid_smem<J>(c);
   if (sm <= 44 * 1024) grid_JB<J, 5>(c, mode, vis, sm, s);
+  else if (sm <= 56 * 1024) grid_JB<J, 4>(c, mode, vis, sm, s);
   else grid_JB<J, 3>(c, mode, vis, sm, s);
 }
 
