@@ -550,8 +550,9 @@ int enqueue_sdmm_step(purify_ctx* c, purify_sdmm_state* st, cudaStream_t s) {
   } else {
     // Psi^H x_hat with the soft threshold and dual update fused (u1 = r1 - z1), then x1 = Psi u1
     SaraProxArgs pa{st->z1, st->u1, st->w};
-    TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, st->side));
-    TRY(sara_synthesis(c, st->u1, st->x1, st->side));
+    int f1_parts = 0;
+    TRY(sara_analysis(c, st->xhat, nullptr, kSaraProx, pa, st->side, &f1_parts));
+    TRY(sara_synthesis(c, st->u1, st->x1, st->side, f1_parts));
   }
   TRY_CUDA(cudaEventRecord(st->ev_join, st->side));
   // i = 2: s2 = Phi x_hat and the l2 norms (FP64), the ball projection, z2 and v = u2 - s2

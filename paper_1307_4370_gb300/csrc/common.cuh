@@ -504,9 +504,13 @@ struct SaraProxArgs {
   float2* u1;
   const float* w;       // NULL = 1
 };
+// Prox mode: the analysis leaves per-block partials of f1 (in the kCntF1
+// slot) and returns their count in *f1_parts; the synthesis launched next
+// with that count forms f1 and zeta in an extra block (no ticket, no fence in
+// the analysis).  *f1_parts = 0: the analysis formed them itself.
 int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode,
-                  const SaraProxArgs& pa, cudaStream_t s);
-int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s);
+                  const SaraProxArgs& pa, cudaStream_t s, int* f1_parts = nullptr);
+int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s, int f1_parts = 0);
 void make_daubechies(WaveletFilters& wf);
 
 // vecops.cu

@@ -31,6 +31,7 @@ struct LevelGeom {
   float scale;  // 1 / sqrt(q)
   int first;    // analysis: first level (its f1 total replaces the previous one)
   int dirac;    // analysis, first level: plane of the Dirac basis handled by the CTAs with z = nb, or -1
+  int f1_off;   // analysis, prox mode: index of this launch's first f1 partial
 };
 
 struct BasisList {
@@ -284,16 +285,26 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
     }
   }
   if (MODE == kSaraProx) {
-    double f1d = (double)f1, tot;
-    if (reduce_last_block<1>(&f1d, partials + kCntF1 * 2 * kMaxPartials, &sc->counter[kCntF1], &tot)) {
-      sc->f1 = G.first ? tot : sc->f1 + tot;
-      if (G.last) {
-        // halting quantity zeta of §4.4 (after the last contribution)
-        const double prev = sc->f1_prev;
-        sc->zeta = (prev != 0.0) ? fabs(sc->f1 - prev) / fabs(prev) : INFINITY;
-        sc->f1_prev = sc->f1;
-      }
-    }
+    // this block's f1 partial; the first synthesis launch adds them all up
+    double f1d = (double)f1;
+    block_reduce<1>(&f1d);
+    if (threadIdx.x == 0)
+      partials[kCntF1 * 2 * kMaxPartials + G.f1_off + blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] =
+          f1d;
+  }
+}
+
+// f1 of §4.4 as the sum of the analysis levels' block partials (in index
+// order), and the halting quantity zeta = |f1 - f1_prev| / f1_prev.
+__device__ __forceinline__ void sara_f1_finish(const double* __restrict__ part, int n, DevScalars* sc) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(&part[i]);
+  block_reduce<1>(&v);
+  if (threadIdx.x == 0) {
+    sc->f1 = v;
+    const double prev = sc->f1_prev;
+    sc->zeta = (prev != 0.0) ? fabs(v - prev) / fabs(prev) : INFINITY;
+    sc->f1_prev = v;
   }
 }
 
@@ -379,8 +390,13 @@ __device__ __forceinline__ void idwt_filter(const float2* LLs, const float2* HLs
 __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ ll_in, int ll_from_plane,
                                                     float2* __restrict__ ll_out, const float2* __restrict__ coef,
                                                     float2* __restrict__ x, int dirac_plane, LevelGeom G,
-                                                    BasisList bl, WaveletFilters wf) {
+                                                    BasisList bl, WaveletFilters wf, const double* f1_part, int f1_n,
+                                                    DevScalars* sc) {
   extern __shared__ float2 sm[];
+  if (f1_n > 0 && (int)blockIdx.z == (int)gridDim.z - 1) {  // the extra slice: block (0, 0) forms f1 and zeta
+    if (blockIdx.x == 0 && blockIdx.y == 0) sara_f1_finish(f1_part, f1_n, sc);
+    return;
+  }
   const int L = G.L, H = L / 2;
   const int TO = G.tile;
   const int K1 = blockIdx.y * 2 * TO, K2 = blockIdx.x * 2 * TO;
@@ -472,6 +488,10 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
   }
 }
 
+__global__ void __launch_bounds__(256) k_f1_finish(const double* __restrict__ part, int n, DevScalars* sc) {
+  sara_f1_finish(part, n, sc);
+}
+
 // Dirac-only synthesis: x = alpha_0 / sqrt(q).
 __global__ void k_dirac_syn(const float2* __restrict__ a, float2* __restrict__ x, int64_t N, float scale) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
@@ -531,7 +551,8 @@ static size_t idwt_smem(int TO, int p) {
 }
 
 int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, const SaraProxArgs& pa,
-                  cudaStream_t s) {
+                  cudaStream_t s, int* f1_parts) {
+  if (f1_parts) *f1_parts = 0;
   int dirac_plane, plane0, nb;
   BasisList bl{};
   basis_layout(c, dirac_plane, plane0, bl, nb);
@@ -553,14 +574,17 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
   }
   int maxp = 1;
   for (int k = 0; k < nb; ++k) maxp = std::max(maxp, bl.p[k]);
+  int f1_off = 0;
   for (int lev = 0; lev < c->levels; ++lev) {
     const int L = c->n >> lev;
     const int H = L / 2;
     const int TI = tile_for(H, nb + (lev == 0 && dirac_plane >= 0 ? 1 : 0), c->sms);
-    LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale, lev == 0, lev == 0 ? dirac_plane : -1};
+    LevelGeom G{TI, c->n, L, nb, plane0, lev == c->levels - 1, scale, lev == 0, lev == 0 ? dirac_plane : -1, f1_off};
     const float2* in = (lev == 0) ? x : c->d_ll[(lev - 1) & 1];
     float2* llo = c->d_ll[lev & 1];
     dim3 grid(H / TI, H / TI, nb + (G.dirac >= 0 ? 1 : 0));
+    f1_off += (int)(grid.x * grid.y * grid.z);
+    if (mode == kSaraProx && f1_off > 2 * kMaxPartials) return PURIFY_E_SIZE;  // the kCntF1 slot holds 2 kMaxPartials
     const size_t sm = dwt_smem(TI, 2 * maxp);
     if (mode == kSaraPlain)
       PURIFY_LAUNCH(c, "dwt_level", s,
@@ -571,10 +595,18 @@ int sara_analysis(purify_ctx* c, const float2* x, float2* alpha, SaraMode mode, 
                     (k_dwt_level<kSaraProx><<<grid, 256, sm, s>>>(in, lev == 0, llo, pa.z1, G, bl, c->wf, pa,
                                                                   c->d_partials, c->d_sc)));
   }
+  if (mode == kSaraProx) {
+    if (f1_parts) {
+      *f1_parts = f1_off;
+    } else {  // no synthesis follows to finish f1: one block does
+      PURIFY_LAUNCH(c, "f1_finish", s,
+                    (k_f1_finish<<<1, 256, 0, s>>>(c->d_partials + kCntF1 * 2 * kMaxPartials, f1_off, c->d_sc)));
+    }
+  }
   return check_cuda(cudaGetLastError());
 }
 
-int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s) {
+int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s, int f1_parts) {
   int dirac_plane, plane0, nb;
   BasisList bl{};
   basis_layout(c, dirac_plane, plane0, bl, nb);
@@ -595,10 +627,14 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
     const bool from_plane = (lev == c->levels - 1);
     const float2* llin = from_plane ? nullptr : c->d_ll[(lev + 1) & 1];
     float2* llo = c->d_ll[lev & 1];
-    dim3 grid(L / (2 * TO), L / (2 * TO), lev == 0 ? 1 : nb);
+    // the first launch (coarsest level) carries one more z slice whose first
+    // block forms f1 and zeta from the analysis partials
+    const int f1n = (lev == c->levels - 1) ? f1_parts : 0;
+    dim3 grid(L / (2 * TO), L / (2 * TO), (lev == 0 ? 1 : nb) + (f1n > 0 ? 1 : 0));
     const size_t sm = idwt_smem(TO, maxp);
     PURIFY_LAUNCH(c, "idwt_level", s,
-                  (k_idwt_level<<<grid, 256, sm, s>>>(llin, from_plane, llo, alpha, x, dirac_plane, G, bl, c->wf)));
+                  (k_idwt_level<<<grid, 256, sm, s>>>(llin, from_plane, llo, alpha, x, dirac_plane, G, bl, c->wf,
+                                                      c->d_partials + kCntF1 * 2 * kMaxPartials, f1n, c->d_sc)));
   }
   return check_cuda(cudaGetLastError());
 }
