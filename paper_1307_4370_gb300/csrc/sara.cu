@@ -297,8 +297,22 @@ __global__ void __launch_bounds__(256) k_dwt_level(const float2* __restrict__ in
 // f1 of §4.4 as the sum of the analysis levels' block partials (in index
 // order), and the halting quantity zeta = |f1 - f1_prev| / f1_prev.
 __device__ __forceinline__ void sara_f1_finish(const double* __restrict__ part, int n, DevScalars* sc) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(&part[i]);
+  // eight independent sums per thread (loads in flight together), in a fixed order
+  constexpr int U = 8;
+  const int nt = blockDim.x;
+  double a[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) a[u] = 0.0;
+  int i = threadIdx.x;
+  for (; i + (U - 1) * nt < n; i += U * nt) {
+    double t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) t[u] = __ldcg(&part[i + u * nt]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] += t[u];
+  }
+  for (; i < n; i += nt) a[0] += __ldcg(&part[i]);
+  double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   block_reduce<1>(&v);
   if (threadIdx.x == 0) {
     sc->f1 = v;
@@ -393,16 +407,19 @@ __global__ void __launch_bounds__(256) k_idwt_level(const float2* __restrict__ l
                                                     BasisList bl, WaveletFilters wf, const double* f1_part, int f1_n,
                                                     DevScalars* sc) {
   extern __shared__ float2 sm[];
-  if (f1_n > 0 && (int)blockIdx.z == (int)gridDim.z - 1) {  // the extra slice: block (0, 0) forms f1 and zeta
+  // with f1 partials to sum, the first z slice is extra (dispatched first, so
+  // that its block (0, 0), which forms f1 and zeta, overlaps the tiles)
+  if (f1_n > 0 && blockIdx.z == 0) {
     if (blockIdx.x == 0 && blockIdx.y == 0) sara_f1_finish(f1_part, f1_n, sc);
     return;
   }
+  const int bz = (int)blockIdx.z - (f1_n > 0 ? 1 : 0);  // the plane slice of this block
   const int L = G.L, H = L / 2;
   const int TO = G.tile;
   const int K1 = blockIdx.y * 2 * TO, K2 = blockIdx.x * 2 * TO;
   // the finest level loops over all planes in one CTA; otherwise one plane per z
-  const int kbeg = G.last ? 0 : blockIdx.z;
-  const int kend = G.last ? G.nb : blockIdx.z + 1;
+  const int kbeg = G.last ? 0 : bz;
+  const int kend = G.last ? G.nb : bz + 1;
   constexpr int kMaxOut = kIdwtMaxOut;
   float2 accum[kMaxOut];
   const int nout = (2 * TO) * (2 * TO);
@@ -627,8 +644,8 @@ int sara_synthesis(purify_ctx* c, const float2* alpha, float2* x, cudaStream_t s
     const bool from_plane = (lev == c->levels - 1);
     const float2* llin = from_plane ? nullptr : c->d_ll[(lev + 1) & 1];
     float2* llo = c->d_ll[lev & 1];
-    // the first launch (coarsest level) carries one more z slice whose first
-    // block forms f1 and zeta from the analysis partials
+    // the first launch (coarsest level) carries one more z slice (the first)
+    // whose first block forms f1 and zeta from the analysis partials
     const int f1n = (lev == c->levels - 1) ? f1_parts : 0;
     dim3 grid(L / (2 * TO), L / (2 * TO), (lev == 0 ? 1 : nb) + (f1n > 0 ? 1 : 0));
     const size_t sm = idwt_smem(TO, maxp);
