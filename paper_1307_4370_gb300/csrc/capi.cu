@@ -310,6 +310,9 @@ void free_ctx(purify_ctx* c) {
 #define PURIFY_DENSE_ENTRIES_PER_CELL 2.0
 #endif
 constexpr double kDenseEntriesPerCell = PURIFY_DENSE_ENTRIES_PER_CELL;
+// ... and one per cell, stored by half, when those stencils fit a quarter of L2
+constexpr double kDenseEntriesPerCellL2 = 1.0;
+constexpr size_t kDenseL2Bytes = (size_t)32 << 20;
 
 // G^T G restricted to the cells of the dense tiles (§5: G^H G, precomputed
 // and stored, to speed up the CG solve): for cell k of tile t and offset d in
@@ -357,6 +360,73 @@ void build_dense_gram(const purify_ctx* c, const purify::GatherPlan& plan, const
         }
       }
       float* out = H.data() + q * (size_t)ND * TT;
+      for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
+    }
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+}
+
+// The same operator stored by half (for small problems, whose stencils stay
+// in L2): G^T G is symmetric, (G^T G)[k][k + d] = (G^T G)[k + d][k], so only
+// the offsets d >= 0 in lexicographic order are kept, NH = J + (J - 1)(2J - 1)
+// of the (2J - 1)^2:
+//   H[t][s(d)][e] = sum over visibilities m of w_m(e) w_m(e + d)
+// for the cells e of the tile extended by J - 1 rows above and J - 1 columns
+// on each side (the cells k - d of the tile's cells k), and
+//   (G^T G X)(k) = sum_{d >= 0} H[s(d)][k] X(k + d) + sum_{d > 0} H[s(d)][k - d] X(k - d).
+// Every visibility whose footprint covers a tile cell is on the tile's list,
+// so every value that equation reads is complete.  Slice order: s = dc for
+// dr = 0, dc = 0 .. J - 1; then s = J + (dr - 1)(2J - 1) + dc + J - 1 for
+// dr = 1 .. J - 1, dc = -(J - 1) .. J - 1.
+void build_dense_gram_half(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
+                           const std::vector<int>& dense, std::vector<float>& H) {
+  const int T = c->tileT, J = c->J, W = T + J - 1, NDW = 2 * J - 1;
+  const int NH = dense_gram_slices(J), EW = T + 2 * (J - 1), EH = T + J - 1, ES = EW * EH;
+  const double beta = kb_beta(J), i0b = std::cyl_bessel_i(0.0, beta);
+  H.assign((size_t)dense.size() * NH * ES, 0.0f);
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    std::vector<double> acc((size_t)NH * ES);
+    for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
+      const int t = dense[q];
+      std::fill(acc.begin(), acc.end(), 0.0);
+      for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
+        const int4 le = entries[e];
+        const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
+        float frf, fcf;
+        std::memcpy(&frf, &le.z, 4);
+        std::memcpy(&fcf, &le.w, 4);
+        double wr[kMaxJ], wc[kMaxJ];
+        for (int a = 0; a < J; ++a) {
+          wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+          wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+        }
+        // every ordered pair of footprint cells (a, b) -> (a2, b2) with a
+        // lexicographically non-negative offset, accumulated at the first cell
+        for (int a = 0; a < J; ++a) {
+          const int er = kr + a;  // extended-region row of the first cell: tile row + J - 1
+          if (er >= EH) continue;
+          for (int b = 0; b < J; ++b) {
+            const int ec = kc + b;  // extended-region column: tile column + J - 1
+            if (ec >= EW) continue;
+            const double wk = wr[a] * wc[b];
+            double* he = acc.data() + (size_t)er * EW + ec;
+            for (int a2 = a; a2 < J; ++a2) {
+              const int dr = a2 - a;
+              for (int b2 = (dr == 0 ? b : 0); b2 < J; ++b2) {
+                const int dc = b2 - b;
+                const int sl = dr == 0 ? dc : J + (dr - 1) * NDW + dc + J - 1;
+                he[(size_t)sl * ES] += wk * wr[a2] * wc[b2];
+              }
+            }
+          }
+        }
+      }
+      float* out = H.data() + q * (size_t)NH * ES;
       for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
     }
   };
@@ -449,10 +519,21 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
   }
   // dense tiles of the Gram pass and their stored G^T G (see build_dense_gram)
   if (st == PURIFY_OK) {
+    // layout: the half stencil, with one entry per cell as the threshold,
+    // when those stencils fit a quarter of L2 (they stay resident across the
+    // CG steps; 256^2 workload: Gram 15.4 -> 12.8 us); the full stencil, two
+    // entries per cell, otherwise (HBM-streamed: 1024^2 half 136.8 us, full
+    // 130.9 us)
+    const size_t half_bytes = (size_t)dense_gram_slices(c->J) * (T + c->J - 1) * (T + 2 * (c->J - 1)) * 4;
+    int n_low = 0;
+    for (int t = 0; t < c->ntiles; ++t)
+      if ((double)(plan.list_off[t + 1] - plan.list_off[t]) > kDenseEntriesPerCellL2 * T * T) ++n_low;
+    c->dense_half = (size_t)n_low * half_bytes <= kDenseL2Bytes ? 1 : 0;
+    const double per_cell = c->dense_half ? kDenseEntriesPerCellL2 : kDenseEntriesPerCell;
     std::vector<int> dense;
     std::vector<char> is_dense(c->ntiles, 0);
     for (int t = 0; t < c->ntiles; ++t)
-      if ((double)(plan.list_off[t + 1] - plan.list_off[t]) > kDenseEntriesPerCell * T * T) {
+      if ((double)(plan.list_off[t + 1] - plan.list_off[t]) > per_cell * T * T) {
         dense.push_back(t);
         is_dense[t] = 1;
       }
@@ -466,7 +547,10 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       std::vector<int4> entries(c->nlist);
       if (cudaMemcpy(entries.data(), c->d_list, c->nlist * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess)
         st = PURIFY_E_CUDA;
-      if (st == PURIFY_OK) build_dense_gram(c, plan, entries, dense, H);
+      if (st == PURIFY_OK) {
+        if (c->dense_half) build_dense_gram_half(c, plan, entries, dense, H);
+        else build_dense_gram(c, plan, entries, dense, H);
+      }
     }
     if (st == PURIFY_OK && ((st = dev_alloc(&c->d_dense_tiles, std::max(1, c->n_dense))) ||
                             (st = dev_alloc(&c->d_gram_chunks, std::max(1, c->n_gram_chunks))) ||

@@ -257,6 +257,8 @@ __host__ __device__ constexpr size_t grid_fixed_bytes(int T, int J) {
 // SM: 139 / 154 us; 44 KB, five: 131 / 154 us; 56 KB, four: 129.5 / 146 us.
 // The gather is latency-bound, so resident warps matter, but smaller chunks
 // split more tiles into several chunks (partial tiles and their merge).
+// offsets d = (dr, dc) >= 0 (lexicographic) of a half G^T G stencil
+__host__ __device__ constexpr int dense_gram_slices(int J) { return J + (J - 1) * (2 * J - 1); }
 #ifndef PURIFY_GRID_SMEM_BUDGET_KB
 #define PURIFY_GRID_SMEM_BUDGET_KB 56
 #endif
@@ -321,7 +323,9 @@ struct purify_ctx {
   // chunks of the remaining tiles (gram_chunks)
   int n_dense;
   int* d_dense_tiles;   // tile of each dense CTA
-  float* d_H;           // n_dense x (2J - 1)^2 x T^2: H[t][d][cell], d = (dr + J - 1)(2J - 1) + dc + J - 1
+  int dense_half;       // 1: d_H holds half stencils (build_dense_gram_half), 0: full ones
+  float* d_H;           // full: n_dense x (2J - 1)^2 x T^2: H[t][d][cell], d = (dr + J - 1)(2J - 1) + dc + J - 1;
+                        // half: n_dense x dense_gram_slices(J) x (T + J - 1)(T + 2J - 2)
   int n_gram_chunks;
   int* d_gram_chunks;   // chunks of the tiles that are not dense
   // degridding work units: (tile, begin, end, -) runs of home visibilities

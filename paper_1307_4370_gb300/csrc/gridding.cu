@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
                                                        int use_tma, DevScalars* sc, int n_dense,
                                                        const int* __restrict__ dense_tiles,
                                                        const float* __restrict__ H,
-                                                       const int* __restrict__ gram_chunks) {
+                                                       const int* __restrict__ gram_chunks, int dense_half) {
   constexpr int NT = kGridThreads;
   constexpr int S = grid_wstride(J);  // [0 wr_0 .. wr_{J-1} 0 | 0 wc_0 .. wc_{J-1} 0 | pad]
   extern __shared__ __align__(128) float4 sm4[];
@@ -327,6 +327,54 @@ __global__ void __launch_bounds__(kGridThreads, MINB) k_grid(float2* __restrict_
       }
     }
     __syncthreads();
+    if (dense && dense_half) {
+      // (G^T G X)(k) = sum_{d >= 0} H[d][k] X(k + d) + sum_{d > 0} H[d][k - d] X(k - d)
+      // over the lexicographically non-negative offsets d (the half stencil,
+      // on the tile extended by J - 1 rows above and J - 1 columns each side);
+      // the slice of one offset serves both terms.  X from the halo.
+      constexpr int NDW = 2 * J - 1, NH = dense_gram_slices(J);
+      const int TT = T * T, lt = lhb + 1;
+      const int EW = T + 2 * (J - 1), ES = EW * (T + J - 1);
+      const float* Ht = H + (size_t)blockIdx.x * NH * ES;
+      for (int k = threadIdx.x; k < TT; k += NT) {
+        const int r = k >> lt, cc = k & (T - 1);
+        const int e0 = (r + J - 1) * EW + cc + J - 1;          // k in the extended region
+        const float2* xk = halo + (r + J - 1) * HWS + cc + J;  // X(k)
+        float2 acc = make_float2(0.f, 0.f);
+        {  // dr = 0, dc = 0 .. J - 1
+          float hf[J], hb[J];
+#pragma unroll
+          for (int dc = 0; dc < J; ++dc) {
+            hf[dc] = __ldg(&Ht[(size_t)dc * ES + e0]);
+            hb[dc] = dc > 0 ? __ldg(&Ht[(size_t)dc * ES + e0 - dc]) : 0.f;
+          }
+#pragma unroll
+          for (int dc = 0; dc < J; ++dc) {
+            acc = caxpy(hf[dc], xk[dc], acc);
+            if (dc > 0) acc = caxpy(hb[dc], xk[-dc], acc);
+          }
+        }
+#pragma unroll 1
+        for (int dr = 1; dr < J; ++dr) {  // dc = -(J - 1) .. J - 1
+          const float* hs = Ht + (size_t)(J + (dr - 1) * NDW) * ES;
+          const float2* xf = xk + dr * HWS - (J - 1);
+          const float2* xb = xk - dr * HWS + (J - 1);
+          float hf[NDW], hb[NDW];
+#pragma unroll
+          for (int u = 0; u < NDW; ++u) {  // u = dc + J - 1
+            hf[u] = __ldg(&hs[(size_t)u * ES + e0]);
+            hb[u] = __ldg(&hs[(size_t)u * ES + e0 - dr * EW - (u - (J - 1))]);
+          }
+#pragma unroll
+          for (int u = 0; u < NDW; ++u) {
+            acc = caxpy(hf[u], xf[u], acc);
+            acc = caxpy(hb[u], xb[-u], acc);
+          }
+        }
+        X[(size_t)(R0 + r) * L + C0 + cc] = acc;
+      }
+      return;
+    }
     if (dense) {
       // (G^T G X)(k) = sum_d H[d][k] X(k + d) over the (2J - 1)^2 offsets, H
       // streamed once per launch (coalesced over the cells), X from the halo
@@ -583,7 +631,7 @@ static void grid_JB(purify_ctx* c, GridIn mode, const float2* vis, size_t sm, cu
                       c->d_tile_slot0, c->d_tile_nchunk,                                                        \
                       c->d_tile_cnt, c->d_slots, c->kb, c->ks, c->L, c->tileT, c->tiles_1d, c->chunk_max,      \
                       c->halo_map, c->halo_map_ok, c->d_sc, c->n_dense, c->d_dense_tiles, c->d_H,             \
-                      c->d_gram_chunks)));                                                                      \
+                      c->d_gram_chunks, c->dense_half)));                                                       \
   } while (0)
   if (mode == kGridPerm) GRD(kGridPerm, "grid", c->d_grid, nullptr);
   else if (mode == kGridSorted) GRD(kGridSorted, "grid", c->d_grid, nullptr);
