@@ -311,7 +311,10 @@ void free_ctx(purify_ctx* c) {
 #endif
 constexpr double kDenseEntriesPerCell = PURIFY_DENSE_ENTRIES_PER_CELL;
 // ... and one per cell, stored by half, when those stencils fit a quarter of L2
-constexpr double kDenseEntriesPerCellL2 = 1.0;
+#ifndef PURIFY_DENSE_ENTRIES_PER_CELL_L2
+#define PURIFY_DENSE_ENTRIES_PER_CELL_L2 1.0
+#endif
+constexpr double kDenseEntriesPerCellL2 = PURIFY_DENSE_ENTRIES_PER_CELL_L2;
 constexpr size_t kDenseL2Bytes = (size_t)32 << 20;
 
 // G^T G restricted to the cells of the dense tiles (§5: G^H G, precomputed
