@@ -6,7 +6,7 @@ Algorithm 1 step 5 solves Q x = sum_i x_i with Q = sum_i L_i^H L_i (§4.3
 eq. qp1, eq. upd1).  With L1 = Psi^H (a Parseval frame), L2 = Phi, L3 = I,
 Q = Phi^H Phi + 2I (§4.4), Hermitian positive definite; §4.4 solves it with
 the conjugate gradient method (Saad 2003).  The paper does not fix the start
-or the step count: this build warm-starts from the previous x-hat and takes a
+or the step count: the reading taken here warm-starts from the previous x-hat and takes a
 fixed number k of steps.  Inner products are Hermitian, <a, b> = a^H b.
 
 Standard CG (Saad 2003, Algorithm 6.18) in complex128:

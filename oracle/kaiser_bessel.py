@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 §5 eq. opmodel builds Phi = G F D Z B with G a compactly supported
 convolutional interpolation kernel in the frequency plane and D the diagonal
 of 1/g_hat, g_hat being the inverse Fourier transform of the continuous
-kernel.  The paper uses a Gaussian kernel; this build uses a Kaiser-Bessel
+kernel.  The paper uses a Gaussian kernel; the reading taken here is a Kaiser-Bessel
 kernel of support J cells, whose transform has a closed form.
 
     g(t)     = I0(beta * sqrt(1 - (2t/J)^2)) / I0(beta),   |t| <= J/2,  else 0

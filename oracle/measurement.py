@@ -8,7 +8,7 @@ Phi = G F D Z B with B the primary beam (the identity in every experiment of
 so N' = 4N), D the diagonal deapodisation 1/g_hat, F the unitary 2-D DFT and
 G the convolutional interpolation onto the continuous frequencies.
 
-Conventions (the paper fixes none of them; these are this build's reading):
+Conventions (the paper fixes none of them; these are the readings taken here):
 
 * image x is n x n, x[r, c] is the pixel at offset l = (r - n/2, c - n/2);
 * a visibility frequency u = (u0, u1) is in radians per pixel, in [-pi, pi)^2,

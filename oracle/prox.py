@@ -12,7 +12,7 @@ not at y.  The projection onto B as defined in §4.3 is
 
     P_B(r) = y + min(1, eps / ||r - y||) (r - y),
 
-and that is what this build computes (identity when r is inside B).
+and that is what is computed here (identity when r is inside B).
 
 For f3 = indicator of the positive orthant (eq. prox3): complex vectors are
 treated as real vectors of twice the length (§4.1), so the orthant of

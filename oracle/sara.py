@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Psi = [Psi_1, ..., Psi_q], here the Dirac basis and the orthonormal
 Daubechies bases db1..db8 (q = 9, D = 9N).  §4.4 needs Psi Psi^H = I (a
 Parseval frame) so that Q = Phi^H Phi + 2I; the plain concatenation of nine
-orthonormal bases has Psi Psi^H = 9 I, so this build scales it by
+orthonormal bases has Psi Psi^H = 9 I, so it is scaled here by
 1/sqrt(q).  Hence
 
     Psi^H x   = (1/sqrt q) [x; W_1 x; ...; W_8 x]            (analysis, C^N -> C^D)

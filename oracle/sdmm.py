@@ -19,7 +19,7 @@ l2 ball B around y, f3 = indicator of the positive orthant.  Algorithm 1
   9          x_i(t) = L_i^H (r_i(t) - z_i(t))
  11      stop if the halting test holds
 
-Readings of what the paper leaves open (this build's choices):
+Readings of what the paper leaves open (the choices made here):
 
 * x is kept complex, as in eq. cvx2 (x in C^N); the image is Re x_hat.
 * x_hat(0) = 0, so r_i(0) = 0 and x_i(0) = 0.

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 §6: visibilities are corrupted by i.i.d. complex Gaussian noise at an input
 SNR, ISNR = 20 log10(||y0|| / ||n||) = 30 dB, and the bound of eq. delta is
 eps^2 = (2M + 4 sqrt(M)) sigma_n^2 / 2, sigma_n^2 / 2 being the variance of
-the real and of the imaginary part.  This build sets
+the real and of the imaginary part.  The reading taken here sets
 sigma_n = ||y0|| / sqrt(M) * 10^(-ISNR/20) (so the expected ||n|| matches the
 ISNR) and scales unit-variance draws by it.  SNR of a reconstruction is
 20 log10(||x|| / ||x - x_hat||) (§6).

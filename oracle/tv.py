@@ -39,7 +39,7 @@ from __future__ import annotations
 
 import numpy as np
 
-FGP_ITERS = 20  # inner iterations per prox (the paper gives none; this build's reading)
+FGP_ITERS = 20  # inner iterations per prox (the paper gives none; the reading taken here)
 
 
 def grad(x: np.ndarray):
