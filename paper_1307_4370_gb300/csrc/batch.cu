@@ -10,6 +10,7 @@
 // persistent kernel with software grid barriers between the phases was the
 // other candidate; on this GPU its barriers cost more than the graph's kernel
 // boundaries, so the batch is a graph.)
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -81,7 +82,7 @@ int capture(purify_batch* b) {
 
 extern "C" {
 
-int purify_batch_create(purify_batch** out, purify_ctx* const* ctxs, purify_sdmm_state* const* states,
+static int purify_batch_create_impl(purify_batch** out, purify_ctx* const* ctxs, purify_sdmm_state* const* states,
                         int32_t count) {
   if (!out) return PURIFY_E_INVALID_ARG;
   *out = nullptr;
@@ -116,6 +117,16 @@ int purify_batch_create(purify_batch** out, purify_ctx* const* ctxs, purify_sdmm
   }
   *out = b;
   return PURIFY_OK;
+}
+
+int purify_batch_create(purify_batch** out, purify_ctx* const* ctxs, purify_sdmm_state* const* states,
+                        int32_t count) {
+  // host containers may throw; no exception crosses the C ABI
+  try {
+    return purify_batch_create_impl(out, ctxs, states, count);
+  } catch (const std::bad_alloc&) {
+    return PURIFY_E_ALLOC;
+  }
 }
 
 int purify_batch_step(purify_batch* b, int32_t iters, purify_stream_t stream) {

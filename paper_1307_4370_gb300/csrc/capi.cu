@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -325,52 +326,62 @@ constexpr size_t kDenseL2Bytes = (size_t)32 << 20;
 // visibility whose footprint covers a cell of the tile is on the tile's list,
 // so (G^T G X)(k) = sum_d H[t][d][k] X(k + d) exactly.  Built in double on
 // the host, one tile per thread of a small pool, and stored as float.
-void build_dense_gram(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
+int build_dense_gram(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
                       const std::vector<int>& dense, std::vector<float>& H) {
   const int T = c->tileT, J = c->J, W = T + J - 1, ND = (2 * J - 1) * (2 * J - 1), TT = T * T;
   const double beta = kb_beta(J), i0b = std::cyl_bessel_i(0.0, beta);
   H.assign((size_t)dense.size() * ND * TT, 0.0f);
   std::atomic<size_t> next{0};
+  std::atomic<bool> failed{false};
   auto work = [&]() {
-    std::vector<double> acc((size_t)ND * TT);
-    for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
-      const int t = dense[q];
-      std::fill(acc.begin(), acc.end(), 0.0);
-      for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
-        const int4 le = entries[e];
-        const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
-        float frf, fcf;
-        std::memcpy(&frf, &le.z, 4);
-        std::memcpy(&fcf, &le.w, 4);
-        double wr[kMaxJ], wc[kMaxJ];
-        for (int a = 0; a < J; ++a) {
-          wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
-          wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
-        }
-        for (int a = 0; a < J; ++a) {
-          const int r = kr - (J - 1) + a;
-          if (r < 0 || r >= T) continue;
-          for (int b = 0; b < J; ++b) {
-            const int cc = kc - (J - 1) + b;
-            if (cc < 0 || cc >= T) continue;
-            const double wk = wr[a] * wc[b];
-            double* hk = acc.data() + r * T + cc;
-            for (int a2 = 0; a2 < J; ++a2) {
-              const int drow = (a2 - a + J - 1) * (2 * J - 1) - b + J - 1;
-              for (int b2 = 0; b2 < J; ++b2) hk[(size_t)(drow + b2) * TT] += wk * wr[a2] * wc[b2];
+    try {
+      std::vector<double> acc((size_t)ND * TT);
+      for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
+        const int t = dense[q];
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
+          const int4 le = entries[e];
+          const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
+          float frf, fcf;
+          std::memcpy(&frf, &le.z, 4);
+          std::memcpy(&fcf, &le.w, 4);
+          double wr[kMaxJ], wc[kMaxJ];
+          for (int a = 0; a < J; ++a) {
+            wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+            wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+          }
+          for (int a = 0; a < J; ++a) {
+            const int r = kr - (J - 1) + a;
+            if (r < 0 || r >= T) continue;
+            for (int b = 0; b < J; ++b) {
+              const int cc = kc - (J - 1) + b;
+              if (cc < 0 || cc >= T) continue;
+              const double wk = wr[a] * wc[b];
+              double* hk = acc.data() + r * T + cc;
+              for (int a2 = 0; a2 < J; ++a2) {
+                const int drow = (a2 - a + J - 1) * (2 * J - 1) - b + J - 1;
+                for (int b2 = 0; b2 < J; ++b2) hk[(size_t)(drow + b2) * TT] += wk * wr[a2] * wc[b2];
+              }
             }
           }
         }
+        float* out = H.data() + q * (size_t)ND * TT;
+        for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
       }
-      float* out = H.data() + q * (size_t)ND * TT;
-      for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
+    } catch (...) {  // no exception leaves a worker thread (nor the C ABI)
+      failed = true;
     }
   };
   const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   std::vector<std::thread> pool;
-  for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  try {
+    for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  } catch (...) {
+    // fewer threads: the queue of tiles is shared, the started ones and this one finish it
+  }
   work();
   for (auto& th : pool) th.join();
+  return failed ? PURIFY_E_ALLOC : PURIFY_OK;
 }
 
 // The same operator stored by half (for small problems, whose stencils stay
@@ -385,59 +396,69 @@ void build_dense_gram(const purify_ctx* c, const purify::GatherPlan& plan, const
 // so every value that equation reads is complete.  Slice order: s = dc for
 // dr = 0, dc = 0 .. J - 1; then s = J + (dr - 1)(2J - 1) + dc + J - 1 for
 // dr = 1 .. J - 1, dc = -(J - 1) .. J - 1.
-void build_dense_gram_half(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
+int build_dense_gram_half(const purify_ctx* c, const purify::GatherPlan& plan, const std::vector<int4>& entries,
                            const std::vector<int>& dense, std::vector<float>& H) {
   const int T = c->tileT, J = c->J, W = T + J - 1, NDW = 2 * J - 1;
   const int NH = dense_gram_slices(J), EW = T + 2 * (J - 1), EH = T + J - 1, ES = EW * EH;
   const double beta = kb_beta(J), i0b = std::cyl_bessel_i(0.0, beta);
   H.assign((size_t)dense.size() * NH * ES, 0.0f);
   std::atomic<size_t> next{0};
+  std::atomic<bool> failed{false};
   auto work = [&]() {
-    std::vector<double> acc((size_t)NH * ES);
-    for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
-      const int t = dense[q];
-      std::fill(acc.begin(), acc.end(), 0.0);
-      for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
-        const int4 le = entries[e];
-        const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
-        float frf, fcf;
-        std::memcpy(&frf, &le.z, 4);
-        std::memcpy(&fcf, &le.w, 4);
-        double wr[kMaxJ], wc[kMaxJ];
-        for (int a = 0; a < J; ++a) {
-          wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
-          wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
-        }
-        // every ordered pair of footprint cells (a, b) -> (a2, b2) with a
-        // lexicographically non-negative offset, accumulated at the first cell
-        for (int a = 0; a < J; ++a) {
-          const int er = kr + a;  // extended-region row of the first cell: tile row + J - 1
-          if (er >= EH) continue;
-          for (int b = 0; b < J; ++b) {
-            const int ec = kc + b;  // extended-region column: tile column + J - 1
-            if (ec >= EW) continue;
-            const double wk = wr[a] * wc[b];
-            double* he = acc.data() + (size_t)er * EW + ec;
-            for (int a2 = a; a2 < J; ++a2) {
-              const int dr = a2 - a;
-              for (int b2 = (dr == 0 ? b : 0); b2 < J; ++b2) {
-                const int dc = b2 - b;
-                const int sl = dr == 0 ? dc : J + (dr - 1) * NDW + dc + J - 1;
-                he[(size_t)sl * ES] += wk * wr[a2] * wc[b2];
+    try {
+      std::vector<double> acc((size_t)NH * ES);
+      for (size_t q = next.fetch_add(1); q < dense.size(); q = next.fetch_add(1)) {
+        const int t = dense[q];
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int e = plan.list_off[t]; e < plan.list_off[t + 1]; ++e) {
+          const int4 le = entries[e];
+          const int kr = le.y / W, kc = le.y - kr * W;  // footprint start + (J - 1), relative to the tile
+          float frf, fcf;
+          std::memcpy(&frf, &le.z, 4);
+          std::memcpy(&fcf, &le.w, 4);
+          double wr[kMaxJ], wc[kMaxJ];
+          for (int a = 0; a < J; ++a) {
+            wr[a] = interp_g((double)frf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+            wc[a] = interp_g((double)fcf + J / 2 - 1 - a, J, c->kernel, beta, i0b);
+          }
+          // every ordered pair of footprint cells (a, b) -> (a2, b2) with a
+          // lexicographically non-negative offset, accumulated at the first cell
+          for (int a = 0; a < J; ++a) {
+            const int er = kr + a;  // extended-region row of the first cell: tile row + J - 1
+            if (er >= EH) continue;
+            for (int b = 0; b < J; ++b) {
+              const int ec = kc + b;  // extended-region column: tile column + J - 1
+              if (ec >= EW) continue;
+              const double wk = wr[a] * wc[b];
+              double* he = acc.data() + (size_t)er * EW + ec;
+              for (int a2 = a; a2 < J; ++a2) {
+                const int dr = a2 - a;
+                for (int b2 = (dr == 0 ? b : 0); b2 < J; ++b2) {
+                  const int dc = b2 - b;
+                  const int sl = dr == 0 ? dc : J + (dr - 1) * NDW + dc + J - 1;
+                  he[(size_t)sl * ES] += wk * wr[a2] * wc[b2];
+                }
               }
             }
           }
         }
+        float* out = H.data() + q * (size_t)NH * ES;
+        for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
       }
-      float* out = H.data() + q * (size_t)NH * ES;
-      for (size_t i = 0; i < acc.size(); ++i) out[i] = (float)acc[i];
+    } catch (...) {  // no exception leaves a worker thread (nor the C ABI)
+      failed = true;
     }
   };
   const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   std::vector<std::thread> pool;
-  for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  try {
+    for (unsigned i = 1; i < hw; ++i) pool.emplace_back(work);
+  } catch (...) {
+    // fewer threads: the queue of tiles is shared, the started ones and this one finish it
+  }
   work();
   for (auto& th : pool) th.join();
+  return failed ? PURIFY_E_ALLOC : PURIFY_OK;
 }
 
 // Visibility table: sort by the grid tile of the first footprint cell and
@@ -550,10 +571,9 @@ int setup_visibilities(purify_ctx* c, const float* uv_in, cudaStream_t s) {
       std::vector<int4> entries(c->nlist);
       if (cudaMemcpy(entries.data(), c->d_list, c->nlist * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess)
         st = PURIFY_E_CUDA;
-      if (st == PURIFY_OK) {
-        if (c->dense_half) build_dense_gram_half(c, plan, entries, dense, H);
-        else build_dense_gram(c, plan, entries, dense, H);
-      }
+      if (st == PURIFY_OK)
+        st = c->dense_half ? build_dense_gram_half(c, plan, entries, dense, H)
+                           : build_dense_gram(c, plan, entries, dense, H);
     }
     if (st == PURIFY_OK && ((st = dev_alloc(&c->d_dense_tiles, std::max(1, c->n_dense))) ||
                             (st = dev_alloc(&c->d_gram_chunks, std::max(1, c->n_gram_chunks))) ||
@@ -710,7 +730,7 @@ const char* purify_last_error(void) {
   return t_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(t_last_cuda_error);
 }
 
-int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purify_stream_t stream) {
+static int purify_create_impl(purify_ctx** out, const purify_desc* d, const float* uv, purify_stream_t stream) {
   if (!out) return PURIFY_E_INVALID_ARG;
   *out = nullptr;
   if (!d || !uv) return PURIFY_E_INVALID_ARG;
@@ -791,10 +811,24 @@ int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purif
   }
   if ((st = fft_prepare(c)) != PURIFY_OK) return fail(st);
   encode_halo_map(c);
-  if ((st = setup_visibilities(c, uv, s)) != PURIFY_OK) return fail(st);
+  try {
+    st = setup_visibilities(c, uv, s);
+  } catch (const std::bad_alloc&) {  // host vectors of the plan and the stencils
+    st = PURIFY_E_ALLOC;
+  }
+  if (st != PURIFY_OK) return fail(st);
   // shared memory above 48 KB needs an opt-in per kernel; sizes here stay below it
   *out = c;
   return PURIFY_OK;
+}
+
+int purify_create(purify_ctx** out, const purify_desc* d, const float* uv, purify_stream_t stream) {
+  // host containers may throw; no exception crosses the C ABI
+  try {
+    return purify_create_impl(out, d, uv, stream);
+  } catch (const std::bad_alloc&) {
+    return PURIFY_E_ALLOC;
+  }
 }
 
 void purify_destroy(purify_ctx* c) {
@@ -1091,7 +1125,7 @@ int purify_prox_tv(purify_ctx* c, const float* in, const float* w, float lambda,
   return tv_prox(c, (const float2*)in, w, lambda, iters, (float2*)out, (cudaStream_t)stream);
 }
 
-int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, const int64_t* offsets,
+static int purify_sdmm_set_blocks_impl(purify_ctx* c, purify_sdmm_state* st, int32_t R, const int64_t* offsets,
                            const double* eps, purify_stream_t stream) {
   if (!c || !st || st->ctx != c || R < 0 || R > kMaxBlocks) return PURIFY_E_INVALID_ARG;
   const int64_t M = c->M;
@@ -1146,6 +1180,16 @@ int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, cons
   st->nblocks = R;
   st->nbchunks = (int)chunks.size();
   return PURIFY_OK;
+}
+
+int purify_sdmm_set_blocks(purify_ctx* c, purify_sdmm_state* st, int32_t R, const int64_t* offsets,
+                           const double* eps, purify_stream_t stream) {
+  // host containers may throw; no exception crosses the C ABI
+  try {
+    return purify_sdmm_set_blocks_impl(c, st, R, offsets, eps, stream);
+  } catch (const std::bad_alloc&) {
+    return PURIFY_E_ALLOC;
+  }
 }
 
 int purify_sdmm_step(purify_ctx* c, purify_sdmm_state* st, purify_stream_t stream) {
@@ -1352,7 +1396,7 @@ int purify_profile_enable(purify_ctx* c, int on) {
   return PURIFY_OK;
 }
 
-int purify_profile_collect(purify_ctx* c, int32_t max_entries, char* names, int64_t* launches, double* ms,
+static int purify_profile_collect_impl(purify_ctx* c, int32_t max_entries, char* names, int64_t* launches, double* ms,
                            int32_t* n_entries) {
   if (!c || max_entries < 0 || !n_entries || (max_entries > 0 && (!names || !launches || !ms)))
     return PURIFY_E_INVALID_ARG;
@@ -1388,6 +1432,16 @@ int purify_profile_collect(purify_ctx* c, int32_t max_entries, char* names, int6
   c->prof.recs.clear();
   c->prof.used = 0;
   return PURIFY_OK;
+}
+
+int purify_profile_collect(purify_ctx* c, int32_t max_entries, char* names, int64_t* launches, double* ms,
+                           int32_t* n_entries) {
+  // host containers may throw; no exception crosses the C ABI
+  try {
+    return purify_profile_collect_impl(c, max_entries, names, launches, ms, n_entries);
+  } catch (const std::bad_alloc&) {
+    return PURIFY_E_ALLOC;
+  }
 }
 
 uint64_t purify_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
