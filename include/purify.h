@@ -131,9 +131,15 @@ typedef struct {
  * the gridding adjoint and its stored gather walk (one 32-bit item per
  * visibility and 2 x 2 cell block its footprint meets, about 12 per
  * visibility for J = 6, so ~50 bytes of device memory per visibility besides
- * the grids and tables); this call synchronises `stream`.  PURIFY_E_SIZE if a
- * gridding work unit does not fit the walk's encoding (not reached for the
- * supported sizes), PURIFY_E_ALLOC if device memory runs out.
+ * the grids and tables).  For the grid tiles whose lists are dense it also
+ * computes G^T G restricted to them (§5: G^H G precomputed for the CG
+ * solve), on the host in double with a pool of threads, and keeps it on the
+ * device as float stencils: (2J - 1)^2 values per cell, or about half that
+ * when the stencils fit a quarter of L2 (at most 4 (2J - 1)^2 bytes per grid
+ * cell of the dense tiles; 200 MB for the 1024 x 1024, M = 2^21 workload).
+ * This call synchronises `stream`.  PURIFY_E_SIZE if a gridding work unit
+ * does not fit the walk's encoding (not reached for the supported sizes),
+ * PURIFY_E_ALLOC if device or host memory runs out.
  * *out receives the context, or NULL on failure. */
 int purify_create(purify_ctx** out, const purify_desc* desc, const float* uv,
                   purify_stream_t stream);
