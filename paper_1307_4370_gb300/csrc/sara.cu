@@ -9,7 +9,9 @@
 // bases and the Dirac plane in the same CTA, so x is written once.  In prox
 // mode the analysis epilogue applies the weighted soft threshold of §4.4
 // eq. prox1 and the dual update of Algorithm 1 steps 7-9 to each final
-// coefficient as it is produced, so alpha itself is never stored.
+// coefficient as it is produced, so alpha itself is never stored; each
+// block leaves one FP64 partial of f1, and the first synthesis launch that
+// follows sums them into f1 and the halting quantity zeta (§4.4).
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -29,7 +31,7 @@ struct LevelGeom {
   int plane0;   // index of the first wavelet plane in the coefficient array
   int last;     // analysis: last level (LL goes to the plane); synthesis: finest level
   float scale;  // 1 / sqrt(q)
-  int first;    // analysis: first level (its f1 total replaces the previous one)
+  int first;    // analysis: first level
   int dirac;    // analysis, first level: plane of the Dirac basis handled by the CTAs with z = nb, or -1
   int f1_off;   // analysis, prox mode: index of this launch's first f1 partial
 };
