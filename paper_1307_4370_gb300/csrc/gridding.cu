@@ -161,6 +161,11 @@ __global__ void __launch_bounds__(256) k_degrid(const float2* __restrict__ X, co
 // stores a partial tile and the last chunk to finish adds the partials in
 // chunk order.  Every cell is written once and the result does not depend
 // on scheduling.
+// The Gram form (G^T G applied to a grid, one per CG step) runs the same
+// gather after degridding each entry from a staged halo of the input grid;
+// its dense tiles instead apply a stored stencil of G^T G per cell (the full
+// (2J - 1)^2 offsets, or the offsets d >= 0 of the symmetric operator on the
+// tile extended by J - 1 cells; built at set-up, build_dense_gram*).
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
