@@ -73,3 +73,15 @@ def test_traffic_record_follows_the_kernel_source(tmp_path, monkeypatch):
     assert bench.dram_traffic("sdmm256", "nosuch") is None
     (csrc / "gridding.cu").write_text("kernel v2\n")
     assert bench.dram_traffic("sdmm256", "grid") is None
+
+
+def test_gram_algorithmic_bytes():
+    """The roofline's algorithmic bytes of the Gram pass (G^T G per CG step):
+    the grid read and the grid written (2 x (2n)^2 complex64 = 8Nc) and the
+    frequencies once (8 B per visibility); for the 1024^2, M = 2^21 workload
+    83,886,080 B, for 256^2, M = 65536, 4,718,592 B."""
+    import bench
+    from paper_1307_4370_gb300 import inputs
+
+    assert bench.algorithmic_bytes(inputs.WORKLOADS["sdmm1024"])["gram"] == 83886080
+    assert bench.algorithmic_bytes(inputs.WORKLOADS["sdmm256"])["gram"] == 4718592
